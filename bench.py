@@ -1,0 +1,434 @@
+#!/usr/bin/env python
+"""Benchmark of the fused D3Q19 BGK lattice update on GB300.
+
+Default workload: 3D periodic Taylor-Green vortex, 256^3 lattice, FP32
+populations (stored as f - w), tau = 0.55, u0 = 0.05, k = 2*pi/256 -- the
+configuration the MLUPS metric is quoted on.  One bench step = one
+lb_step(1) (one fused stream-collide launch over all 16.8 M cells) plus, every
+``--check-every`` steps and once at the end, the FP64 mass/momentum
+reduction used as the divergence check.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun, one rank per GPU; the lattice update does not
+shard here (replicas: every rank advances its own lattice, no collective on
+the data path) and value = all ranks' cell updates / max-over-ranks time.
+
+The reference arm (--impl reference) times the FP64 CPU oracle on the host
+cores, each step a bounded sample (a z-slab of the same lattice).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "D3Q19 MLUPS & fraction of HBM roofline; batched-serve p50/p99 vs plain FP32 launches"
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def bytes_per_update(storage: str) -> int:
+    """Algorithmic bytes per lattice update: 19 reads + 19 writes + 1 flag byte."""
+    return 2 * 19 * STORAGE_BYTES[storage] + 1
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", choices=list(STORAGE_BYTES), default="f32")
+    ap.add_argument("--n", type=int, default=256, help="lattice edge (default 256)")
+    ap.add_argument("--kernel", type=int, default=0, help="step kernel variant (0 = library choice)")
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--check-every", type=int, default=100)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------- distributed
+class Dist:
+    """Rank bookkeeping; a process group only when WORLD_SIZE > 1."""
+
+    def __init__(self, backend=None):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = False
+        if self.world > 1:
+            import torch.distributed as dist
+            if backend is None:
+                import torch
+                backend = "nccl" if torch.cuda.is_available() else "gloo"
+            self.backend = backend
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend=backend)
+            self.pg = True
+
+    def device_tensor(self, v):
+        import torch
+        dev = f"cuda:{self.local_rank}" if getattr(self, "backend", "gloo") == "nccl" else "cpu"
+        return torch.tensor([float(v)], dtype=torch.float64, device=dev)
+
+    def barrier(self):
+        if self.pg:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return float(v)
+        import torch.distributed as dist
+        t = self.device_tensor(v)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v: float) -> float:
+        if not self.pg:
+            return float(v)
+        import torch.distributed as dist
+        t = self.device_tensor(v)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+def aggregate_replicas(dist: Dist, cells_per_rank: float, steps: int, seconds_local: float):
+    """Whole-job throughput of independent replicas: all ranks' updates over
+    the slowest rank's time.  Returns (MLUPS, max seconds)."""
+    t = dist.max(seconds_local)
+    total = dist.sum(cells_per_rank * steps)
+    return total / t / 1e6, t
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, enabled=True):
+        self.gpu = gpu_index
+        self.enabled = enabled
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        if not self.enabled:
+            return
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        return self.summary()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def kernel_source_hash() -> str:
+    """Hash of the CUDA sources; a committed ncu traffic figure is only
+    reported while it matches the kernels being timed."""
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_2409_16781_gb300", "csrc")
+    for name in sorted(os.listdir(cs)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(cs, name), "rb") as fh:
+                h.update(name.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def ncu_traffic(profile_key: str):
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken
+    on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        rec = d.get(profile_key)
+        if rec and rec.get("source_hash") == kernel_source_hash():
+            return rec.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def tgv_inputs(n):
+    from paper_2409_16781_gb300 import workloads as W
+    return W.taylor_green_fields(n, n, n, u0=0.05)
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args, dist: Dist):
+    import numpy as np
+    import torch
+
+    from paper_2409_16781_gb300 import Lattice
+
+    dev = torch.device("cuda", dist.local_rank)
+    torch.cuda.set_device(dev)
+    n = args.n
+    N = n ** 3
+    tau = 0.55
+    stream = torch.cuda.current_stream(dev)
+    rho0, u0 = tgv_inputs(n)
+    lat = Lattice(n, n, n, tau, storage=args.storage, device=dev, stream=stream,
+                  kernel=args.kernel, block=args.block)
+    lat.init_fields(rho0, u0)
+
+    launches_per_check = 2  # reduction kernel + finalize kernel
+    for _ in range(args.warmup):
+        lat.step(1)
+    lat.totals()
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dist.local_rank, enabled=not args.no_clocks and dist.local_rank == 0)
+    n_checks = 0
+    dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    t_start.record(stream)
+    for k in range(K):
+        ev[k][0].record(stream)
+        lat.step(1)
+        ev[k][1].record(stream)
+        if args.check_every > 0 and (k + 1) % args.check_every == 0 and k + 1 < K:
+            lat.totals()
+            n_checks += 1
+    mass, mom = lat.totals()
+    n_checks += 1
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    clock_summary = clocks.stop()
+    seconds = t_start.elapsed_time(t_end) / 1e3
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kernel_ms = statistics.mean(step_ms)
+    value, t_max = aggregate_replicas(dist, N, K, seconds)
+
+    # end-to-end through the C ABI with host buffers: upload the initial
+    # fields from pinned memory, K steps, download rho and u.
+    e2e = None
+    if not args.no_e2e:
+        rho_h = torch.from_numpy(np.ascontiguousarray(rho0)).pin_memory()
+        u_h = torch.from_numpy(np.ascontiguousarray(u0)).pin_memory()
+        rho_out = torch.empty_like(rho_h).pin_memory()
+        u_out = torch.empty_like(u_h).pin_memory()
+        lat.sync()
+        dist.barrier()
+        t0 = time.perf_counter()
+        lat.lib.lb_init_fields(lat.handle, rho_h.data_ptr(), u_h.data_ptr())
+        lat.step(K)
+        st = lat.lib.lb_moments(lat.handle, rho_out.data_ptr(), u_out.data_ptr())
+        t1 = time.perf_counter()
+        assert st == 0
+        dist.barrier()
+        e2e_val, _ = aggregate_replicas(dist, N, K, t1 - t0)
+        e2e = {"value": round(e2e_val, 1), "unit": "MLUPS",
+               "h2d_bytes_per_step": int(32 * N / K), "d2h_bytes_per_step": int(32 * N / K),
+               "what": "lb_init_fields(host rho,u) + lb_step(K) + lb_moments(host rho,u), pinned host buffers"}
+
+    peak, peak_kind = measured_peaks()
+    bpu = bytes_per_update(args.storage)
+    achieved = bpu * N / (kernel_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+            "traffic": ncu_traffic(f"step_{args.storage}_tgv{n}"),
+            "algorithmic_bytes_per_launch": bpu * N, "kernel": "lb step kernel",
+            "kernel_ms_mean": round(kernel_ms, 5), "kernel_ms_median": round(statistics.median(step_ms), 5)}
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": dist.world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": round(t_max * 1e3 / K, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f64": "f64", "f32": "f32", "f16s": "f16", "bf16s": "bf16"}[args.storage],
+        "data": "synthetic",
+        "config": {"workload": f"taylor-green vortex {n}^3, D3Q19 BGK, {args.storage} populations "
+                               f"(f - w), tau={tau}, u0=0.05, k=2pi/{n}",
+                   "lattice": [n, n, n], "storage": args.storage, "tau": tau,
+                   "check_every": args.check_every,
+                   "l2": f"no flush: working set {2 * 19 * STORAGE_BYTES[args.storage] * N / 1e9:.2f} GB "
+                         "> 129 MB L2",
+                   "parallelism": "replicas" if dist.world > 1 else "single"},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": K + launches_per_check * n_checks,
+        "clocks": clock_summary,
+        "mass_drift_rel": abs(mass - N) / N,
+    }
+    lat.close()
+    return line
+
+
+# ---------------------------------------------------------------- oracle
+def oracle_slab_run(n, planes, steps):
+    """Run the FP64 oracle for `steps` steps on an n x n x planes slab of the
+    Taylor-Green lattice; returns (seconds, cells)."""
+    import oracle as O
+    from paper_2409_16781_gb300 import workloads as W
+    rho, u = W.taylor_green_fields(n, n, n, u0=0.05)
+    L = O.Lattice(n, n, planes, 0.55)
+    L.init_fields(rho[:planes], u[:, :planes])
+    t0 = time.perf_counter()
+    L.step(steps)
+    return time.perf_counter() - t0, n * n * planes
+
+
+def oracle_threads():
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v else (os.cpu_count() or 1)
+
+
+def cpu_baseline(n, budget_s=12.0):
+    """Oracle MLUPS on a bounded sample: an n x n x 16 slab, as many steps as
+    fit in about budget_s seconds (at least 2)."""
+    planes = 16
+    t1, cells = oracle_slab_run(n, planes, 1)
+    steps = max(2, min(200, int(budget_s / max(t1, 1e-3))))
+    t, cells = oracle_slab_run(n, planes, steps)
+    return {"value": round(cells * steps / t / 1e6, 2), "unit": "MLUPS", "cores": oracle_threads(),
+            "kind": "oracle",
+            "sample": f"{steps} steps of a {n}x{n}x{planes} slab of the {n}^3 Taylor-Green lattice "
+                      f"(FP64 C oracle, OpenMP over z)"}
+
+
+def run_reference(args, dist: Dist):
+    n = args.n
+    # calibrate: one step on an 8-plane slab, then size the per-step sample
+    t_cal, cells_cal = oracle_slab_run(n, 8, 1)
+    rate = cells_cal / max(t_cal, 1e-6)           # cells per second
+    budget = 60.0                                  # seconds for the timed steps
+    planes = int(max(1, min(n, budget * rate / max(1, args.steps) / (n * n))))
+    import oracle as O
+    from paper_2409_16781_gb300 import workloads as W
+    rho, u = W.taylor_green_fields(n, n, n, u0=0.05)
+    L = O.Lattice(n, n, planes, 0.55)
+    L.init_fields(rho[:planes], u[:, :planes])
+    for _ in range(args.warmup):
+        L.step(1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        L.step(1)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    cells = n * n * planes
+    value = cells * args.steps / total / 1e6
+    sample = (f"each step: one oracle update of a {n}x{n}x{planes} slab ({cells} cells) of the "
+              f"{n}^3 Taylor-Green lattice, FP64 C oracle, OpenMP over z")
+    return {
+        "metric": METRIC, "value": round(value, 3), "unit": "MLUPS", "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total * 1e3 / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": f"taylor-green vortex {n}^3, D3Q19 BGK, tau=0.55, u0=0.05, k=2pi/{n}",
+                   "lattice": [n, n, n], "storage": args.storage, "parallelism": "single"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": oracle_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args, _single())))
+        return 0
+    dist = Dist()
+    try:
+        line = run_ours(args, dist)
+        if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(args.n)
+        elif dist.rank == 0:
+            line["cpu_baseline"] = None
+        if dist.rank == 0:
+            print(json.dumps(line), flush=True)
+    finally:
+        dist.close()
+    return 0
+
+
+def _single():
+    d = Dist.__new__(Dist)
+    d.rank, d.world, d.local_rank, d.pg = 0, int(os.environ.get("WORLD_SIZE", "1")), 0, False
+    return d
+
+
+if __name__ == "__main__":
+    sys.exit(main())

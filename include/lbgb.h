@@ -1,0 +1,167 @@
+/*
+ * lbgb.h -- C ABI of the GB300 D3Q19 lattice-Boltzmann library (liblbgb.so).
+ *
+ * The library advances a 3D lattice with the fused stream-and-collide BGK
+ * update of arXiv 2409.16781 (Sec. 2, Eq. 1-3; fused pull with two
+ * population arrays, Sec. 3.1; structure-of-arrays populations, Sec. 3.1;
+ * lid-driven cavity walls and moving lid, Sec. 3.3), extended from the
+ * paper's D2Q9 to the D3Q19 velocity set (the paper's Sec. 6 names the 3D
+ * extension and mixed precision as future work).
+ *
+ * Conventions shared by every call
+ *  - Every call returns an lb_status value (0 = LB_OK, negative = error).
+ *    A failed call leaves the handle valid (except lb_destroy, which always
+ *    releases it).  lb_last_error() gives a one-line description of the most
+ *    recent failure on this thread.
+ *  - Host buffers passed in are owned by the caller and are only read or
+ *    written during the call.  Device buffers passed in (lb_create_in,
+ *    lb_moments_device) are owned by the caller and must outlive their use.
+ *  - Grid: nx, ny, nz >= 1, nx*ny*nz < 2^31 cells.  A scalar field has N =
+ *    nx*ny*nz entries with cell index x + nx*(y + ny*z) (x fastest, the
+ *    column-major order of Sec. 4.2).  A vector field u is SoA: u[a*N + cell],
+ *    a = 0,1,2 for x,y,z.  Populations are q-major: f[i*N + cell].
+ *  - The domain wraps periodically on all six faces; walls are cells
+ *    flagged LB_WALL or LB_LID.
+ *  - Velocity order (fixed): i = 0 rest; 1..6 = +x,-x,+y,-y,+z,-z;
+ *    7..18 = (1,1,0),(-1,-1,0),(1,-1,0),(-1,1,0),(1,0,1),(-1,0,-1),
+ *    (1,0,-1),(-1,0,1),(0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1).  Directions
+ *    2k-1 and 2k are opposite.  Weights 1/3, 1/18 (axes), 1/36 (diagonals).
+ *  - Work is issued asynchronously on the lattice's stream; calls that
+ *    return data to host memory synchronise that stream before returning.
+ */
+#ifndef LBGB_H
+#define LBGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LB_Q 19
+
+typedef struct lb_lattice lb_lattice; /* opaque */
+
+typedef enum {
+    LB_OK = 0,
+    LB_EINVAL = -1,    /* bad argument (sizes, tau <= 1/2, flag values, NULL) */
+    LB_ENOMEM = -2,    /* device allocation failed or buffer too small */
+    LB_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
+    LB_EDIVERGED = -4, /* non-finite or non-positive density found */
+    LB_ETIMEOUT = -5,  /* a bounded device-side wait gave up */
+    LB_EBUSY = -6      /* resource in use (batch capacity reached) */
+} lb_status;
+
+/* Population storage (the paper's precision modes, Sec. 3.1.1).  The "S"
+ * forms store the deviation f_i - w_i; all math is FP32 except LB_F64,
+ * which stores and computes in FP64.  LB_F32 also stores f_i - w_i. */
+typedef enum {
+    LB_F64 = 0,   /* "Double": FP64 storage, FP64 math            */
+    LB_F32 = 1,   /* "Single": FP32 storage, FP32 math            */
+    LB_F16S = 2,  /* "Mixed1": FP16 storage of f - w, FP32 math   */
+    LB_BF16S = 3  /* BF16 storage of f - w, FP32 math             */
+} lb_storage;
+
+/* Cell flags (uint8 per cell). */
+enum { LB_FLUID = 0, LB_WALL = 1, LB_LID = 2 };
+
+typedef struct lb_options {
+    int storage;       /* lb_storage; default LB_F32 */
+    int kernel;        /* step kernel variant: 0 = library's choice */
+    int block;         /* threads per block of the step kernel; 0 = choice */
+    int reserved0;
+    double force[3];   /* body force per unit mass g (Guo forcing, the S_i
+                          of Eq. 1); default 0 */
+    void *stream;      /* cudaStream_t to issue work on; NULL = default */
+    int reserved[8];
+} lb_options;
+
+/* Fill *opt with the defaults (FP32, no force, default stream). */
+void lb_default_options(lb_options *opt);
+
+/* The library's velocity set: c[3*i + a], w[i], i in the order above.
+ * Returns LB_Q. */
+int lb_velocity_set(int *c, double *w);
+
+/* Bytes of device memory one lattice needs (populations A and B, cell
+ * codes, host-transfer staging and reduction scratch).  0 on bad sizes. */
+size_t lb_bytes_required(int nx, int ny, int nz, const lb_options *opt);
+
+/* Create a lattice (Sec. 3.3 use cases; lb_create(nx,ny,nz,tau,u_lid,flags)
+ * of the problem statement).
+ *   tau    BGK relaxation time, omega = 1/tau of Eq. 1; must be > 1/2.
+ *   u_lid  velocity of LB_LID cells (NULL = 0); halfway bounce-back off a
+ *          LID source adds 6 w_i (c_i . u_lid) (wall density 1).
+ *   flags  host, N bytes, values LB_FLUID/LB_WALL/LB_LID, copied at create;
+ *          NULL = all fluid.
+ *   opt    NULL = defaults.
+ * The library allocates lb_bytes_required() bytes of device memory with
+ * cudaMalloc; the populations start at rest, f = w (rho = 1, u = 0).
+ * Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA; *out is NULL on error. */
+int lb_create(lb_lattice **out, int nx, int ny, int nz, double tau,
+              const double *u_lid, const uint8_t *flags, const lb_options *opt);
+
+/* As lb_create, but all device memory comes from the caller's buffer
+ * (device pointer, 256-byte aligned, at least lb_bytes_required() bytes),
+ * which must stay valid until lb_destroy.  Used by the Python binding so
+ * that PyTorch owns the allocation. */
+int lb_create_in(lb_lattice **out, int nx, int ny, int nz, double tau,
+                 const double *u_lid, const uint8_t *flags, const lb_options *opt,
+                 void *device_buffer, size_t bytes);
+
+/* Set every cell to the equilibrium f^eq(rho, u) of Eq. 2-3.
+ *   rho  host, N doubles (NULL = 1);  u  host, 3N doubles SoA (NULL = 0). */
+int lb_init_fields(lb_lattice *h, const double *rho, const double *u);
+
+/* Advance n >= 0 time steps: each is one fused pull-collide launch
+ * (Eq. 1 with the boundary rules) from array A into B, then A <-> B.
+ * Asynchronous on the lattice's stream. */
+int lb_step(lb_lattice *h, int n);
+
+/* Macroscopic fields of the current state: rho and u (half-force shifted,
+ * u = (sum_i f_i c_i)/rho + g/2) of the streamed populations at every fluid
+ * cell; solid cells report rho = 0, u = 0.
+ *   rho  host, N doubles;  u  host, 3N doubles SoA.  Either may be NULL. */
+int lb_moments(lb_lattice *h, double *rho, double *u);
+
+/* As lb_moments, into device buffers (N and 3N doubles), asynchronous. */
+int lb_moments_device(lb_lattice *h, double *rho_dev, double *u_dev);
+
+/* FP64 totals over fluid cells: mass = sum rho, mom = sum rho u.  Computed
+ * on the device with FP64 accumulators and a fixed reduction order (the
+ * result is bitwise reproducible).  Returns LB_EDIVERGED (after filling
+ * the outputs) when a fluid cell has a non-finite or non-positive rho. */
+int lb_totals(lb_lattice *h, double *mass, double *mom);
+
+/* Copy the post-collision populations (array A: the state after the last
+ * step) to/from host FP64, q-major f[i*N + cell], library velocity order.
+ * Values are exact conversions of the stored values (set: rounded to the
+ * storage type, to nearest even, as deviations f - w for the S forms). */
+int lb_get_populations(lb_lattice *h, double *f);
+int lb_set_populations(lb_lattice *h, const double *f);
+
+/* Populations of n listed cells (cell indices in [0, N)): out[k*19 + i].
+ * For sampled checks on lattices too large to copy whole. */
+int lb_get_populations_at(lb_lattice *h, const int64_t *cells, int n, double *out);
+
+/* Wait for all work issued on the lattice's stream. */
+int lb_sync(lb_lattice *h);
+
+/* Query: dims[3], storage, steps taken since create. */
+int lb_query(lb_lattice *h, int *dims, int *storage, int64_t *steps);
+
+/* Release the lattice (frees library-allocated device memory).  Safe on
+ * NULL. */
+int lb_destroy(lb_lattice *h);
+
+/* Static description of a status code. */
+const char *lb_status_string(int status);
+
+/* Description of the last failure on the calling thread ("" if none). */
+const char *lb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBGB_H */

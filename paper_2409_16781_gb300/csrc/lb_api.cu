@@ -1,0 +1,429 @@
+// lb_api.cu -- the C ABI of liblbgb (declared in include/lbgb.h): argument
+// validation, device-memory layout of a lattice, chunked host transfers and
+// the time-step loop.  All arithmetic runs in the kernels of lb_kernels.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lbgb.h"
+#include "lb_internal.h"
+
+using namespace lbgb;
+
+struct lb_lattice {
+    int nx, ny, nz;
+    int64_t N, ps;
+    int storage, sbytes;
+    double tau, ulid[3], g[3];
+    void* base;
+    bool owns;
+    size_t bytes;
+    void* pop[2];  // pop[cur] holds the current post-collision array A
+    int cur;
+    uint8_t* code;
+    double* partials;
+    double* tot_out;
+    void* staging;
+    size_t staging_bytes;
+    cudaStream_t stream;
+    int kernel, block;
+    int64_t steps;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int status, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int status, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(LB_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr size_t ALIGN = 256;
+inline size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+    int64_t N, ps;
+    size_t pop_bytes, code_off, part_off, tot_off, stage_off, stage_bytes, total;
+};
+
+bool valid_dims(int nx, int ny, int nz) {
+    if (nx < 1 || ny < 1 || nz < 1) return false;
+    const int64_t N = (int64_t)nx * ny * nz;
+    return N < (int64_t(1) << 31);
+}
+
+Layout layout_for(int nx, int ny, int nz, int storage) {
+    Layout L{};
+    L.N = (int64_t)nx * ny * nz;
+    L.ps = (int64_t)round_up((size_t)L.N, 128);
+    L.pop_bytes = round_up((size_t)Q * L.ps * storage_bytes(storage), ALIGN);
+    size_t off = 2 * L.pop_bytes;
+    L.code_off = off;
+    off += round_up((size_t)L.N, ALIGN);
+    L.part_off = off;
+    off += round_up((size_t)totals_blocks(L.N) * 6 * sizeof(double), ALIGN);
+    L.tot_off = off;
+    off += ALIGN;
+    // staging for host transfers: FP64 populations of up to the whole lattice,
+    // capped at 32 MiB, at least 64 KiB (one cell of populations is 152 B).
+    size_t want = (size_t)L.N * Q * sizeof(double);
+    if (want > (size_t(32) << 20)) want = size_t(32) << 20;
+    if (want < (size_t(64) << 10)) want = size_t(64) << 10;
+    L.stage_off = off;
+    L.stage_bytes = round_up(want, ALIGN);
+    off += L.stage_bytes;
+    L.total = off;
+    return L;
+}
+
+lb_options defaults() {
+    lb_options o;
+    memset(&o, 0, sizeof o);
+    o.storage = LB_F32;
+    return o;
+}
+
+LatticeParams params_of(const lb_lattice* h) {
+    LatticeParams p;
+    p.nx = h->nx;
+    p.ny = h->ny;
+    p.nz = h->nz;
+    p.N = h->N;
+    p.ps = h->ps;
+    p.omega = 1.0 / h->tau;
+    for (int a = 0; a < 3; ++a) {
+        p.g[a] = h->g[a];
+        p.ulid[a] = h->ulid[a];
+    }
+    return p;
+}
+
+int64_t chunk_cells(const lb_lattice* h, size_t bytes_per_cell) {
+    int64_t c = (int64_t)(h->staging_bytes / bytes_per_cell);
+    return c < 1 ? 1 : c;
+}
+
+int create_common(lb_lattice** out, int nx, int ny, int nz, double tau, const double* u_lid, const uint8_t* flags,
+                  const lb_options* opt, void* buffer, size_t bytes) {
+    if (!out) return fail(LB_EINVAL, "lb_create: out is NULL");
+    *out = nullptr;
+    lb_options o = opt ? *opt : defaults();
+    if (!valid_dims(nx, ny, nz)) return fail(LB_EINVAL, "lb_create: bad dims %d x %d x %d", nx, ny, nz);
+    if (!(tau > 0.5) || !std::isfinite(tau)) return fail(LB_EINVAL, "lb_create: tau must be > 1/2 (got %g)", tau);
+    if (o.storage < LB_F64 || o.storage > LB_BF16S) return fail(LB_EINVAL, "lb_create: bad storage %d", o.storage);
+    for (int a = 0; a < 3; ++a) {
+        if (!std::isfinite(o.force[a])) return fail(LB_EINVAL, "lb_create: non-finite force");
+        if (u_lid && !std::isfinite(u_lid[a])) return fail(LB_EINVAL, "lb_create: non-finite u_lid");
+    }
+    const Layout L = layout_for(nx, ny, nz, o.storage);
+    if (flags) {
+        for (int64_t c = 0; c < L.N; ++c)
+            if (flags[c] > LB_LID) return fail(LB_EINVAL, "lb_create: flag %d at cell %lld", flags[c], (long long)c);
+    }
+    if (buffer) {
+        if (bytes < L.total) return fail(LB_ENOMEM, "lb_create_in: buffer %zu < required %zu", bytes, L.total);
+        if ((uintptr_t)buffer % ALIGN) return fail(LB_EINVAL, "lb_create_in: buffer not 256-byte aligned");
+    }
+    lb_lattice* h = new (std::nothrow) lb_lattice();
+    if (!h) return fail(LB_ENOMEM, "lb_create: host allocation failed");
+    h->nx = nx;
+    h->ny = ny;
+    h->nz = nz;
+    h->N = L.N;
+    h->ps = L.ps;
+    h->storage = o.storage;
+    h->sbytes = storage_bytes(o.storage);
+    h->tau = tau;
+    for (int a = 0; a < 3; ++a) {
+        h->ulid[a] = u_lid ? u_lid[a] : 0.0;
+        h->g[a] = o.force[a];
+    }
+    h->stream = (cudaStream_t)o.stream;
+    h->kernel = o.kernel;
+    h->block = o.block;
+    h->bytes = L.total;
+    if (buffer) {
+        h->base = buffer;
+        h->owns = false;
+    } else {
+        cudaError_t e = cudaMalloc(&h->base, L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return fail(LB_ENOMEM, "lb_create: cudaMalloc(%zu): %s", L.total, cudaGetErrorString(e));
+        }
+        h->owns = true;
+    }
+    char* b = (char*)h->base;
+    h->pop[0] = b;
+    h->pop[1] = b + L.pop_bytes;
+    h->cur = 0;
+    h->code = (uint8_t*)(b + L.code_off);
+    h->partials = (double*)(b + L.part_off);
+    h->tot_out = (double*)(b + L.tot_off);
+    h->staging = b + L.stage_off;
+    h->staging_bytes = L.stage_bytes;
+    h->steps = 0;
+
+    // flags -> codes (through the staging area, in chunks of whole lattice)
+    int rc = LB_OK;
+    cudaError_t e = cudaSuccess;
+    if (flags) {
+        // the classifier needs the whole flag field; stage it in the B array
+        // (not yet initialised) when it does not fit the staging area
+        uint8_t* dflags = (size_t)L.N <= h->staging_bytes ? (uint8_t*)h->staging : (uint8_t*)h->pop[1];
+        e = cudaMemcpyAsync(dflags, flags, (size_t)L.N, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = launch_classify(dflags, h->code, nx, ny, nz, h->stream);
+    } else {
+        e = cudaMemsetAsync(h->code, 0, (size_t)L.N, h->stream);
+    }
+    if (e != cudaSuccess) rc = cuda_fail(e, "lb_create: flags");
+    if (rc == LB_OK) {
+        e = launch_init(h->storage, h->pop[0], h->pop[1], h->ps, nullptr, nullptr, 0, 0, h->N, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "lb_create: init");
+    }
+    if (rc != LB_OK) {
+        if (h->owns) cudaFree(h->base);
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lb_default_options(lb_options* opt) {
+    if (opt) *opt = defaults();
+}
+
+int lb_velocity_set(int* c, double* w) {
+    for (int i = 0; i < Q; ++i) {
+        if (c) {
+            c[3 * i + 0] = D3Q19::cx(i);
+            c[3 * i + 1] = D3Q19::cy(i);
+            c[3 * i + 2] = D3Q19::cz(i);
+        }
+        if (w) w[i] = D3Q19::w(i);
+    }
+    return Q;
+}
+
+size_t lb_bytes_required(int nx, int ny, int nz, const lb_options* opt) {
+    const int storage = opt ? opt->storage : LB_F32;
+    if (!valid_dims(nx, ny, nz) || storage < LB_F64 || storage > LB_BF16S) return 0;
+    return layout_for(nx, ny, nz, storage).total;
+}
+
+int lb_create(lb_lattice** out, int nx, int ny, int nz, double tau, const double* u_lid, const uint8_t* flags,
+              const lb_options* opt) {
+    return create_common(out, nx, ny, nz, tau, u_lid, flags, opt, nullptr, 0);
+}
+
+int lb_create_in(lb_lattice** out, int nx, int ny, int nz, double tau, const double* u_lid, const uint8_t* flags,
+                 const lb_options* opt, void* device_buffer, size_t bytes) {
+    if (!device_buffer) return fail(LB_EINVAL, "lb_create_in: device_buffer is NULL");
+    return create_common(out, nx, ny, nz, tau, u_lid, flags, opt, device_buffer, bytes);
+}
+
+int lb_init_fields(lb_lattice* h, const double* rho, const double* u) {
+    if (!h) return fail(LB_EINVAL, "lb_init_fields: NULL handle");
+    const size_t per_cell = (rho ? 8 : 0) + (u ? 24 : 0);
+    if (per_cell == 0) {
+        cudaError_t e = launch_init(h->storage, h->pop[0], h->pop[1], h->ps, nullptr, nullptr, 0, 0, h->N, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        return e == cudaSuccess ? LB_OK : cuda_fail(e, "lb_init_fields");
+    }
+    const int64_t chunk = chunk_cells(h, per_cell);
+    double* st = (double*)h->staging;
+    for (int64_t c0 = 0; c0 < h->N; c0 += chunk) {
+        const int64_t cnt = (h->N - c0 < chunk) ? h->N - c0 : chunk;
+        double* drho = rho ? st : nullptr;
+        double* du = u ? st + (rho ? cnt : 0) : nullptr;
+        cudaError_t e = cudaSuccess;
+        if (rho) e = cudaMemcpyAsync(drho, rho + c0, cnt * 8, cudaMemcpyHostToDevice, h->stream);
+        for (int a = 0; a < 3 && u && e == cudaSuccess; ++a)
+            e = cudaMemcpyAsync(du + a * cnt, u + a * h->N + c0, cnt * 8, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = launch_init(h->storage, h->pop[h->cur], h->pop[1 - h->cur], h->ps, drho, du, cnt, c0, cnt, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "lb_init_fields");
+    }
+    return LB_OK;
+}
+
+int lb_step(lb_lattice* h, int n) {
+    if (!h) return fail(LB_EINVAL, "lb_step: NULL handle");
+    if (n < 0) return fail(LB_EINVAL, "lb_step: n < 0");
+    const LatticeParams p = params_of(h);
+    for (int t = 0; t < n; ++t) {
+        cudaError_t e = launch_step(h->storage, h->kernel, h->pop[h->cur], h->pop[1 - h->cur], h->code, p, h->block,
+                                    h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "lb_step");
+        h->cur = 1 - h->cur;
+        h->steps++;
+    }
+    return LB_OK;
+}
+
+int lb_moments_device(lb_lattice* h, double* rho_dev, double* u_dev) {
+    if (!h) return fail(LB_EINVAL, "lb_moments_device: NULL handle");
+    cudaError_t e = launch_moments(h->storage, h->pop[h->cur], h->code, params_of(h), rho_dev, u_dev, h->N, 0, h->N,
+                                   h->stream);
+    return e == cudaSuccess ? LB_OK : cuda_fail(e, "lb_moments_device");
+}
+
+int lb_moments(lb_lattice* h, double* rho, double* u) {
+    if (!h) return fail(LB_EINVAL, "lb_moments: NULL handle");
+    if (!rho && !u) return LB_OK;
+    const int64_t chunk = chunk_cells(h, 32);
+    double* st = (double*)h->staging;
+    const LatticeParams p = params_of(h);
+    for (int64_t c0 = 0; c0 < h->N; c0 += chunk) {
+        const int64_t cnt = (h->N - c0 < chunk) ? h->N - c0 : chunk;
+        cudaError_t e = launch_moments(h->storage, h->pop[h->cur], h->code, p, st, st + cnt, cnt, c0, cnt, h->stream);
+        if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho + c0, st, cnt * 8, cudaMemcpyDeviceToHost, h->stream);
+        for (int a = 0; a < 3 && u && e == cudaSuccess; ++a)
+            e = cudaMemcpyAsync(u + a * h->N + c0, st + (1 + a) * cnt, cnt * 8, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "lb_moments");
+    }
+    return LB_OK;
+}
+
+int lb_totals(lb_lattice* h, double* mass, double* mom) {
+    if (!h) return fail(LB_EINVAL, "lb_totals: NULL handle");
+    double out[5];
+    cudaError_t e = launch_totals(h->storage, h->pop[h->cur], h->code, params_of(h), h->partials, h->tot_out,
+                                  h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->tot_out, sizeof out, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lb_totals");
+    if (mass) *mass = out[0];
+    if (mom)
+        for (int a = 0; a < 3; ++a) mom[a] = out[1 + a];
+    if (out[4] != 0.0 || !std::isfinite(out[0]))
+        return fail(LB_EDIVERGED, "lb_totals: %.0f fluid cells with non-finite or non-positive density", out[4]);
+    return LB_OK;
+}
+
+int lb_get_populations(lb_lattice* h, double* f) {
+    if (!h || !f) return fail(LB_EINVAL, "lb_get_populations: NULL argument");
+    const int64_t chunk = chunk_cells(h, Q * 8);
+    double* st = (double*)h->staging;
+    for (int64_t c0 = 0; c0 < h->N; c0 += chunk) {
+        const int64_t cnt = (h->N - c0 < chunk) ? h->N - c0 : chunk;
+        cudaError_t e = launch_get_pops(h->storage, h->pop[h->cur], h->ps, c0, cnt, st, h->stream);
+        for (int i = 0; i < Q && e == cudaSuccess; ++i)
+            e = cudaMemcpyAsync(f + i * h->N + c0, st + i * cnt, cnt * 8, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "lb_get_populations");
+    }
+    return LB_OK;
+}
+
+int lb_set_populations(lb_lattice* h, const double* f) {
+    if (!h || !f) return fail(LB_EINVAL, "lb_set_populations: NULL argument");
+    const int64_t chunk = chunk_cells(h, Q * 8);
+    double* st = (double*)h->staging;
+    for (int64_t c0 = 0; c0 < h->N; c0 += chunk) {
+        const int64_t cnt = (h->N - c0 < chunk) ? h->N - c0 : chunk;
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < Q && e == cudaSuccess; ++i)
+            e = cudaMemcpyAsync(st + i * cnt, f + i * h->N + c0, cnt * 8, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = launch_set_pops(h->storage, h->pop[h->cur], h->pop[1 - h->cur], h->ps, c0, cnt, st, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "lb_set_populations");
+    }
+    return LB_OK;
+}
+
+int lb_get_populations_at(lb_lattice* h, const int64_t* cells, int n, double* out) {
+    if (!h || (n > 0 && (!cells || !out))) return fail(LB_EINVAL, "lb_get_populations_at: NULL argument");
+    if (n < 0) return fail(LB_EINVAL, "lb_get_populations_at: n < 0");
+    for (int k = 0; k < n; ++k)
+        if (cells[k] < 0 || cells[k] >= h->N)
+            return fail(LB_EINVAL, "lb_get_populations_at: cell %lld out of range", (long long)cells[k]);
+    // cell indices (rounded up to ALIGN) followed by the gathered values
+    int64_t chunk = (int64_t)((h->staging_bytes - ALIGN) / (8 + Q * 8));
+    if (chunk < 1) chunk = 1;
+    char* st = (char*)h->staging;
+    for (int64_t k0 = 0; k0 < n; k0 += chunk) {
+        const int cnt = (int)((n - k0 < chunk) ? n - k0 : chunk);
+        int64_t* dcells = (int64_t*)st;
+        double* dout = (double*)(st + round_up((size_t)cnt * 8, ALIGN));
+        cudaError_t e = cudaMemcpyAsync(dcells, cells + k0, (size_t)cnt * 8, cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = launch_gather_pops(h->storage, h->pop[h->cur], h->ps, dcells, cnt, dout, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out + k0 * Q, dout, (size_t)cnt * Q * 8, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "lb_get_populations_at");
+    }
+    return LB_OK;
+}
+
+int lb_sync(lb_lattice* h) {
+    if (!h) return fail(LB_EINVAL, "lb_sync: NULL handle");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? LB_OK : cuda_fail(e, "lb_sync");
+}
+
+int lb_query(lb_lattice* h, int* dims, int* storage, int64_t* steps) {
+    if (!h) return fail(LB_EINVAL, "lb_query: NULL handle");
+    if (dims) {
+        dims[0] = h->nx;
+        dims[1] = h->ny;
+        dims[2] = h->nz;
+    }
+    if (storage) *storage = h->storage;
+    if (steps) *steps = h->steps;
+    return LB_OK;
+}
+
+int lb_destroy(lb_lattice* h) {
+    if (!h) return LB_OK;
+    int rc = LB_OK;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "lb_destroy: sync");
+    if (h->owns) {
+        e = cudaFree(h->base);
+        if (e != cudaSuccess && rc == LB_OK) rc = cuda_fail(e, "lb_destroy: cudaFree");
+    }
+    delete h;
+    return rc;
+}
+
+const char* lb_status_string(int status) {
+    switch (status) {
+        case LB_OK: return "ok";
+        case LB_EINVAL: return "invalid argument";
+        case LB_ENOMEM: return "out of device memory";
+        case LB_ECUDA: return "CUDA error";
+        case LB_EDIVERGED: return "simulation diverged";
+        case LB_ETIMEOUT: return "device wait timed out";
+        case LB_EBUSY: return "resource busy";
+        default: return "unknown status";
+    }
+}
+
+const char* lb_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// lb_common.cuh -- D3Q19 lattice constants and storage traits for the
+// sm_103a kernels of liblbgb.
+//
+// The velocity set is the 3D extension of the paper's D2Q9 (arXiv 2409.16781
+// Sec. 2; 3D named as future work in Sec. 6): rest, the 6 axis neighbours
+// (w = 1/18) and the 12 edge neighbours (w = 1/36), c_s^2 = 1/3, in the order
+// fixed by include/lbgb.h (opposites are 2k-1, 2k).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace lbgb {
+
+constexpr int Q = 19;
+
+struct D3Q19 {
+    __host__ __device__ static constexpr int cx(int i) {
+        constexpr int t[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int cy(int i) {
+        constexpr int t[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int cz(int i) {
+        constexpr int t[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+        return t[i];
+    }
+    __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+};
+
+// Internal per-cell code byte (built from the user's flags at create time):
+//   bits 0-1: own type (0 fluid, 1 wall, 2 lid)
+//   bit 7   : some pull source x - c_i of this cell is solid, so the cell
+//             takes the bounce-back path (interior cells skip the 18
+//             neighbour-flag reads).
+constexpr uint8_t CODE_TYPE = 0x03;
+constexpr uint8_t CODE_NEAR_WALL = 0x80;
+
+// Storage traits: populations are stored as deviations d_i = f_i - w_i.
+template <class S> struct Storage;
+
+template <> struct Storage<double> {
+    using math = double;
+    static constexpr int id = 0;
+    __device__ __forceinline__ static double load(double v) { return v; }
+    __device__ __forceinline__ static double store(double v) { return v; }
+};
+template <> struct Storage<float> {
+    using math = float;
+    static constexpr int id = 1;
+    __device__ __forceinline__ static float load(float v) { return v; }
+    __device__ __forceinline__ static float store(float v) { return v; }
+};
+template <> struct Storage<__half> {
+    using math = float;
+    static constexpr int id = 2;
+    __device__ __forceinline__ static float load(__half v) { return __half2float(v); }
+    __device__ __forceinline__ static __half store(float v) { return __float2half_rn(v); }
+};
+template <> struct Storage<__nv_bfloat16> {
+    using math = float;
+    static constexpr int id = 3;
+    __device__ __forceinline__ static float load(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ __forceinline__ static __nv_bfloat16 store(float v) { return __float2bfloat16_rn(v); }
+};
+
+// Parameters of one lattice as seen by the kernels.
+struct LatticeParams {
+    int nx, ny, nz;
+    int64_t N;        // nx*ny*nz
+    int64_t ps;       // plane stride between populations (elements), >= N
+    double omega;     // 1/tau
+    double g[3];      // body force per unit mass
+    double ulid[3];   // lid velocity
+};
+
+}  // namespace lbgb

@@ -1,0 +1,185 @@
+"""Python binding of one D3Q19 lattice (argument marshalling over the C ABI).
+
+PyTorch provides the device memory (one uint8 tensor handed to
+``lb_create_in``) and the CUDA stream; every step of the computation runs in
+the kernels of liblbgb.so.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+
+Q = L.Q
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def velocity_set():
+    """(c[19,3], w[19]) in the library's order (include/lbgb.h)."""
+    c = np.zeros(57, dtype=np.int32)
+    w = np.zeros(19, dtype=np.float64)
+    L.lib().lb_velocity_set(_dptr(c), _dptr(w))
+    return c.reshape(19, 3).astype(np.int64), w
+
+
+def make_options(storage="f32", force=(0.0, 0.0, 0.0), stream=None, kernel=0, block=0):
+    o = L.LbOptions()
+    L.lib().lb_default_options(ctypes.byref(o))
+    o.storage = L.STORAGE[storage] if isinstance(storage, str) else int(storage)
+    o.kernel = int(kernel)
+    o.block = int(block)
+    for a in range(3):
+        o.force[a] = float(force[a])
+    o.stream = stream
+    return o
+
+
+def bytes_required(nx, ny, nz, storage="f32") -> int:
+    o = make_options(storage)
+    return int(L.lib().lb_bytes_required(int(nx), int(ny), int(nz), ctypes.byref(o)))
+
+
+class Lattice:
+    """A lattice advanced by liblbgb on one GPU.
+
+    Arrays follow the library's layout: scalar fields (nz, ny, nx), vector
+    fields (3, nz, ny, nx), populations (19, nz, ny, nx) in the library's
+    velocity order; flags uint8 (nz, ny, nx) with 0 fluid, 1 wall, 2 lid.
+    """
+
+    def __init__(self, nx, ny, nz, tau, u_lid=(0.0, 0.0, 0.0), flags=None, storage="f32",
+                 force=(0.0, 0.0, 0.0), device=None, stream=None, kernel=0, block=0,
+                 library_memory=False):
+        import torch
+
+        self.lib = L.lib()
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.N = self.nx * self.ny * self.nz
+        self.shape = (self.nz, self.ny, self.nx)
+        self.tau = float(tau)
+        self.storage = storage
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None \
+            else torch.device(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        opts = make_options(storage, force, ctypes.c_void_p(stream.cuda_stream), kernel, block)
+        ulid = (ctypes.c_double * 3)(*[float(v) for v in u_lid])
+        fl = None
+        if flags is not None:
+            fl = np.ascontiguousarray(flags, dtype=np.uint8).reshape(-1)
+            if fl.size != self.N:
+                raise ValueError(f"flags has {fl.size} entries, lattice has {self.N}")
+        self._flags = fl
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            if library_memory:
+                self._buf = None
+                st = self.lib.lb_create(ctypes.byref(h), self.nx, self.ny, self.nz, self.tau, ulid,
+                                        None if fl is None else _dptr(fl), ctypes.byref(opts))
+            else:
+                nbytes = self.lib.lb_bytes_required(self.nx, self.ny, self.nz, ctypes.byref(opts))
+                if nbytes == 0:
+                    raise L.LbError(L.LB_EINVAL, f"bad lattice size {nx}x{ny}x{nz}")
+                self._buf = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+                st = self.lib.lb_create_in(ctypes.byref(h), self.nx, self.ny, self.nz, self.tau, ulid,
+                                           None if fl is None else _dptr(fl), ctypes.byref(opts),
+                                           ctypes.c_void_p(self._buf.data_ptr()), nbytes)
+        L.check(st, "lb_create")
+        self._h = h
+
+    # ------------------------------------------------------------------
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            st = self.lib.lb_destroy(self._h)
+            self._h = None
+            L.check(st, "lb_destroy")
+        self._buf = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------------
+    def init_fields(self, rho=None, u=None):
+        r = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+        uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        if r is not None and r.size != self.N:
+            raise ValueError("rho has the wrong size")
+        if uu is not None and uu.size != 3 * self.N:
+            raise ValueError("u has the wrong size")
+        L.check(self.lib.lb_init_fields(self._h, None if r is None else _dptr(r),
+                                        None if uu is None else _dptr(uu)), "lb_init_fields")
+
+    def step(self, n: int = 1):
+        L.check(self.lib.lb_step(self._h, int(n)), "lb_step")
+
+    def sync(self):
+        L.check(self.lib.lb_sync(self._h), "lb_sync")
+
+    def moments(self):
+        rho = np.empty(self.shape)
+        u = np.empty((3,) + self.shape)
+        L.check(self.lib.lb_moments(self._h, _dptr(rho), _dptr(u)), "lb_moments")
+        return rho, u
+
+    def moments_device(self, rho=None, u=None):
+        """(rho, u) as float64 CUDA tensors, issued on the lattice's stream."""
+        import torch
+        if rho is None:
+            rho = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        if u is None:
+            u = torch.empty((3,) + self.shape, dtype=torch.float64, device=self.device)
+        L.check(self.lib.lb_moments_device(self._h, ctypes.c_void_p(rho.data_ptr()),
+                                           ctypes.c_void_p(u.data_ptr())), "lb_moments_device")
+        return rho, u
+
+    def totals(self, check=True):
+        m = ctypes.c_double()
+        p = (ctypes.c_double * 3)()
+        st = self.lib.lb_totals(self._h, ctypes.byref(m), p)
+        if check:
+            L.check(st, "lb_totals")
+        return m.value, np.array(p[:])
+
+    def populations(self):
+        f = np.empty((Q,) + self.shape)
+        L.check(self.lib.lb_get_populations(self._h, _dptr(f)), "lb_get_populations")
+        return f
+
+    def set_populations(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+        if f.size != Q * self.N:
+            raise ValueError("populations have the wrong size")
+        L.check(self.lib.lb_set_populations(self._h, _dptr(f)), "lb_set_populations")
+
+    def populations_at(self, cells):
+        cells = np.ascontiguousarray(cells, dtype=np.int64).reshape(-1)
+        out = np.empty((cells.size, Q))
+        L.check(self.lib.lb_get_populations_at(self._h, _dptr(cells), int(cells.size), _dptr(out)),
+                "lb_get_populations_at")
+        return out
+
+    def query(self):
+        dims = (ctypes.c_int * 3)()
+        st = ctypes.c_int()
+        steps = ctypes.c_int64()
+        L.check(self.lib.lb_query(self._h, dims, ctypes.byref(st), ctypes.byref(steps)), "lb_query")
+        return tuple(dims), st.value, steps.value

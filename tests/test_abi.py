@@ -1,0 +1,101 @@
+"""The C-ABI library loads and exports every symbol that include/lbgb.h
+declares, and its host-side validation answers without a GPU (CPU only)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2409_16781_gb300 import _lib as L
+from paper_2409_16781_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbgb.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(lb_[a-z_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lb_create", "lb_step", "lb_moments", "lb_destroy", "lb_totals",
+                     "lb_init_fields", "lb_get_populations", "lb_set_populations"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", L.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (lb_\w+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+    assert set(L.SIGNATURES) == set(declared_functions())
+
+
+def test_velocity_set_is_d3q19(lib):
+    from paper_2409_16781_gb300 import velocity_set
+    c, w = velocity_set()
+    gold = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "d3q19_velocity_set.txt")):
+        if line.strip() and not line.startswith("#"):
+            a, b, cc, ww = line.split()
+            num, den = ww.split("/")
+            gold[(int(a), int(b), int(cc))] = int(num) / int(den)
+    assert {tuple(v) for v in c.tolist()} == set(gold)
+    for i in range(19):
+        assert w[i] == gold[tuple(c[i].tolist())]
+    # opposites at (2k-1, 2k) as the header states
+    for k in range(1, 10):
+        assert np.array_equal(c[2 * k - 1], -c[2 * k])
+
+
+def test_bytes_required(lib):
+    from paper_2409_16781_gb300 import bytes_required
+    n = bytes_required(256, 256, 256, "f32")
+    assert n >= 2 * 19 * 256 ** 3 * 4 + 256 ** 3
+    assert bytes_required(256, 256, 256, "f16s") < n < bytes_required(256, 256, 256, "f64")
+    assert bytes_required(0, 4, 4) == 0
+    assert bytes_required(2048, 2048, 1024) == 0  # >= 2^31 cells
+
+
+@pytest.mark.parametrize("args,what", [
+    ((0, 4, 4, 0.6), "zero dim"),
+    ((4, 4, 4, 0.5), "tau = 1/2"),
+    ((4, 4, 4, float("nan")), "tau nan"),
+    ((4, 4, -1, 0.7), "negative dim"),
+])
+def test_create_rejects_bad_arguments(lib, args, what):
+    h = ctypes.c_void_p()
+    st = lib.lb_create(ctypes.byref(h), *args, None, None, None)
+    assert st == L.LB_EINVAL, what
+    assert h.value is None
+    assert lib.lb_last_error().decode()
+
+
+def test_create_rejects_bad_flags(lib):
+    h = ctypes.c_void_p()
+    flags = np.zeros(64, dtype=np.uint8)
+    flags[17] = 3
+    st = lib.lb_create(ctypes.byref(h), 4, 4, 4, 0.7, None,
+                       flags.ctypes.data_as(ctypes.c_void_p), None)
+    assert st == L.LB_EINVAL
+    assert "17" in lib.lb_last_error().decode()
+
+
+def test_null_handle_calls(lib):
+    assert lib.lb_step(None, 1) == L.LB_EINVAL
+    assert lib.lb_moments(None, None, None) == L.LB_EINVAL
+    assert lib.lb_destroy(None) == L.LB_OK
+    assert lib.lb_status_string(L.LB_EDIVERGED) == b"simulation diverged"

@@ -1,0 +1,208 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Tolerances (stated per storage form):
+  f64   : populations, max |f - f_oracle| / |f_oracle| <= 1e-12 over fluid cells
+  f32   : velocity, max |u - u_oracle| / max |u_oracle| <= 1e-5
+  f16s  : velocity, same measure, <= 2e-3
+  bf16s : velocity, same measure, <= 3e-2 (reported form, 8-bit mantissa)
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from parity import fluid_mask, lib_to_oracle_perm, pop_rel_err, to_lib_order, to_oracle_order, vel_err
+from paper_2409_16781_gb300 import Lattice, LbDiverged
+from paper_2409_16781_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+VEL_TOL = {"f32": 1e-5, "f16s": 2e-3, "bf16s": 3e-2}
+
+
+@pytest.fixture(scope="module")
+def perm():
+    return lib_to_oracle_perm()
+
+
+def run_pair(nx, ny, nz, tau, steps, storage, flags=None, u_lid=(0, 0, 0), force=(0, 0, 0),
+             rho0=None, u0=None, kernel=0):
+    ora = O.Lattice(nx, ny, nz, tau, u_lid=u_lid, flags=flags, force=force)
+    if rho0 is not None or u0 is not None:
+        ora.init_fields(rho0, u0)
+    gpu = Lattice(nx, ny, nz, tau, u_lid=u_lid, flags=flags, storage=storage, force=force,
+                  kernel=kernel)
+    if rho0 is not None or u0 is not None:
+        gpu.init_fields(rho0, u0)
+    ora.step(steps)
+    gpu.step(steps)
+    return ora, gpu
+
+
+def check_pair(ora, gpu, storage, perm, flags):
+    mask = fluid_mask(flags, gpu.shape)
+    rho_o, u_o = ora.moments()
+    rho_g, u_g = gpu.moments()
+    if storage == "f64":
+        f_g = gpu.populations()
+        err = pop_rel_err(f_g, to_lib_order(ora.A, perm), mask)
+        assert err <= 1e-12, f"f64 population error {err:.3e}"
+        assert vel_err(u_g, u_o, mask) <= 1e-11
+        assert np.abs(rho_g[mask] - rho_o[mask]).max(initial=0) <= 1e-12
+    else:
+        err = vel_err(u_g, u_o, mask)
+        assert err <= VEL_TOL[storage], f"{storage} velocity error {err:.3e}"
+    # solid cells report zeros
+    assert np.all(rho_g[~mask] == 0) and np.all(u_g[:, ~mask] == 0)
+
+
+STORAGES = ["f64", "f32", "f16s", "bf16s"]
+
+TINY = [
+    # nx, ny, nz, tau, steps, flags-spec, u_lid, force
+    (1, 1, 1, 0.7, 12, None, (0, 0, 0), (1e-4, -2e-4, 3e-4)),
+    (3, 5, 7, 0.65, 20, ("random", 9), (0.05, 0.02, 0.0), (1e-4, 0, -1e-4)),
+    (17, 9, 4, 0.8, 20, ("random", 4), (0.08, 0.0, 0.01), (0, 0, 0)),
+    (33, 5, 3, 0.55, 20, None, (0, 0, 0), (2e-5, 1e-5, 0)),
+    (70, 3, 2, 0.9, 15, ("cavity", 0), (0.1, 0, 0), (0, 0, 0)),
+    (18, 9, 5, 0.6, 20, ("random", 21), (0.05, -0.03, 0.02), (5e-5, 0, 1e-4)),
+    (66, 5, 4, 0.7, 20, ("random", 22), (0.02, 0.0, 0.0), (0, 0, 0)),
+]
+
+KERNELS = [1, 4]
+
+
+def _flags(spec, nx, ny, nz):
+    if spec is None:
+        return None
+    kind, seed = spec
+    if kind == "random":
+        return W.random_flags(nx, ny, nz, seed=seed, p_wall=0.2, p_lid=0.1)
+    return W.cavity_flags(nx, ny, nz)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("storage", STORAGES)
+@pytest.mark.parametrize("case", TINY, ids=lambda c: f"{c[0]}x{c[1]}x{c[2]}")
+def test_tiny_grids(case, storage, kernel, perm):
+    nx, ny, nz, tau, steps, spec, ulid, g = case
+    flags = _flags(spec, nx, ny, nz)
+    rho0, u0 = W.random_fields(nx, ny, nz, seed=nx * 100 + ny * 10 + nz, du=0.06, drho=0.02)
+    ora, gpu = run_pair(nx, ny, nz, tau, steps, storage, flags, ulid, g, rho0, u0, kernel=kernel)
+    check_pair(ora, gpu, storage, perm, flags)
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s"])
+def test_every_variant(storage, kernel, perm):
+    """Every step-kernel variant (cache policies, one or two cells per
+    thread) on a grid with walls, lid and force, odd and even row lengths."""
+    for nx, ny, nz in ((34, 7, 6), (35, 6, 5)):
+        flags = W.random_flags(nx, ny, nz, seed=nx, p_wall=0.15, p_lid=0.1)
+        rho0, u0 = W.random_fields(nx, ny, nz, seed=7, du=0.05, drho=0.02)
+        ora, gpu = run_pair(nx, ny, nz, 0.7, 12, storage, flags, (0.04, 0.01, -0.02), (1e-4, 0, 0),
+                            rho0, u0, kernel=kernel)
+        check_pair(ora, gpu, storage, perm, flags)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("storage", STORAGES)
+def test_cavity_32(storage, kernel, perm):
+    """32^3 lid-driven cavity, tau 0.6, lid (0.1,0,0) on the top plane,
+    rho = 1 at rest, 500 steps (f64: populations to 1e-12)."""
+    n = 32
+    flags = W.cavity_flags(n, n, n)
+    ora, gpu = run_pair(n, n, n, 0.6, 500, storage, flags, (0.1, 0, 0), kernel=kernel)
+    check_pair(ora, gpu, storage, perm, flags)
+    m_o, p_o = ora.totals()
+    m_g, p_g = gpu.totals()
+    if storage == "f64":
+        assert abs(m_g - m_o) <= 1e-12 * m_o
+        assert np.abs(p_g - p_o).max() <= 1e-12 * m_o
+    assert abs(m_g - 30 ** 3) <= (1e-11 if storage == "f64" else 1e-3) * 30 ** 3
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s"])
+def test_taylor_green_64(storage, kernel, perm):
+    n = 64
+    rho0, u0 = W.taylor_green_fields(n, n, n, u0=0.05)
+    ora, gpu = run_pair(n, n, n, 0.55, 100, storage, None, rho0=rho0, u0=u0, kernel=kernel)
+    check_pair(ora, gpu, storage, perm, None)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_porous_channel_small(storage, kernel, perm):
+    nx, ny, nz = 48, 40, 36
+    flags = W.porous_flags(nx, ny, nz, n_spheres=12, r_min=3, r_max=6, seed=2409)
+    ora, gpu = run_pair(nx, ny, nz, 0.8, 200, storage, flags, force=(1e-5, 0, 0), kernel=kernel)
+    check_pair(ora, gpu, storage, perm, flags)
+
+
+def test_zero_steps_and_rest_state():
+    gpu = Lattice(9, 7, 5, 0.6, flags=W.random_flags(9, 7, 5, seed=1), storage="f32")
+    f0 = gpu.populations()
+    gpu.step(0)
+    assert np.array_equal(gpu.populations(), f0)
+    gpu.step(25)  # rest state, no lid motion, no force: deviations stay exactly 0
+    assert np.array_equal(gpu.populations(), f0)
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_populations_roundtrip(storage, perm):
+    nx, ny, nz = 11, 6, 5
+    gpu = Lattice(nx, ny, nz, 0.7, storage=storage)
+    _, w = O.velocity_set()
+    f = W.random_populations(nx, ny, nz, seed=3, w=to_lib_order(w, perm), amp=0.01)
+    gpu.set_populations(f)
+    g1 = gpu.populations()
+    if storage == "f64":
+        assert np.array_equal(g1, f)
+    gpu.set_populations(g1)  # stored values convert exactly both ways
+    assert np.array_equal(gpu.populations(), g1)
+    cells = np.array([0, 7, 66, nx * ny * nz - 1])
+    at = gpu.populations_at(cells)
+    assert np.array_equal(at, g1.reshape(19, -1)[:, cells].T)
+
+
+def test_set_populations_matches_oracle_step(perm):
+    """Arbitrary (non-equilibrium) states: one step from the same populations."""
+    nx, ny, nz = 13, 8, 6
+    flags = W.random_flags(nx, ny, nz, seed=12, p_wall=0.15, p_lid=0.1)
+    _, w = O.velocity_set()
+    f = W.random_populations(nx, ny, nz, seed=5, w=w, amp=0.02)  # oracle order
+    ora = O.Lattice(nx, ny, nz, 0.75, u_lid=(0.03, -0.02, 0.01), flags=flags, force=(1e-4, 0, 2e-4))
+    ora.set_populations(f)
+    gpu = Lattice(nx, ny, nz, 0.75, u_lid=(0.03, -0.02, 0.01), flags=flags, storage="f64",
+                  force=(1e-4, 0, 2e-4))
+    gpu.set_populations(to_lib_order(f, perm))
+    for _ in range(3):
+        ora.step(1)
+        gpu.step(1)
+        err = pop_rel_err(gpu.populations(), to_lib_order(ora.A, perm), fluid_mask(flags, gpu.shape))
+        assert err <= 1e-13
+
+
+def test_totals_flags_divergence(perm):
+    nx, ny, nz = 8, 8, 8
+    gpu = Lattice(nx, ny, nz, 0.7, storage="f32")
+    m, p = gpu.totals()
+    assert m == pytest.approx(512.0, rel=1e-12) and np.abs(p).max() < 1e-12
+    f = gpu.populations()
+    f[3, 2, 2, 2] = np.nan
+    gpu.set_populations(f)
+    with pytest.raises(LbDiverged):
+        gpu.totals()
+
+
+def test_library_owned_memory(perm):
+    """lb_create (library cudaMalloc) and lb_create_in (torch buffer) agree."""
+    n = 12
+    flags = W.cavity_flags(n, n, n)
+    a = Lattice(n, n, n, 0.6, u_lid=(0.1, 0, 0), flags=flags, storage="f64", library_memory=True)
+    b = Lattice(n, n, n, 0.6, u_lid=(0.1, 0, 0), flags=flags, storage="f64")
+    a.step(30)
+    b.step(30)
+    assert np.array_equal(a.populations(), b.populations())
+    a.close()
+    b.close()
