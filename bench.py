@@ -58,6 +58,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use the library default variant instead of the autotuner's choice")
     return ap.parse_args(argv)
 
 
@@ -243,6 +245,9 @@ def run_ours(args, dist: Dist):
     lat = Lattice(n, n, n, tau, storage=args.storage, device=dev, stream=stream,
                   kernel=args.kernel, block=args.block)
     lat.init_fields(rho0, u0)
+    tuned = None
+    if args.kernel == 0 and not args.no_autotune:
+        tuned = lat.autotune(reps=20, cache=False)
 
     launches_per_check = 2  # reduction kernel + finalize kernel
     for _ in range(args.warmup):
@@ -319,6 +324,9 @@ def run_ours(args, dist: Dist):
                                f"(f - w), tau={tau}, u0=0.05, k=2pi/{n}",
                    "lattice": [n, n, n], "storage": args.storage, "tau": tau,
                    "check_every": args.check_every,
+                   "kernel": ({"variant": tuned[0], "block": tuned[1], "chosen_by": "lb_autotune"}
+                              if tuned else {"variant": args.kernel, "block": args.block,
+                                             "chosen_by": "command line"}),
                    "l2": f"no flush: working set {2 * 19 * STORAGE_BYTES[args.storage] * N / 1e9:.2f} GB "
                          "> 129 MB L2",
                    "parallelism": "replicas" if dist.world > 1 else "single"},

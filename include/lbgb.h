@@ -145,6 +145,22 @@ int lb_set_populations(lb_lattice *h, const double *f);
  * For sampled checks on lattices too large to copy whole. */
 int lb_get_populations_at(lb_lattice *h, const int64_t *cells, int n, double *out);
 
+/* Step-kernel choice.  Variants: 0 library default; 1 one cell per thread;
+ * 2, 3 as 1 with streaming / L2-only cache policies; 4, 5 two cells per
+ * thread (even nx); 6, 7 two cells per thread, packed 16-bit registers
+ * (16-bit storage, even nx); 8, 9 four cells per thread, packed 16-bit
+ * (16-bit storage, nx % 4 == 0).  A variant that does not apply to the
+ * lattice runs variant 1.  block = threads per block (0 = default; rounded
+ * down to whole warps). */
+int lb_set_kernel(lb_lattice *h, int variant, int block);
+
+/* Autotuner: time every applicable (variant, block) pair on this lattice
+ * with `reps` launches each (CUDA events on the lattice's stream), keep the
+ * fastest for later lb_step calls and report it (outputs may be NULL).
+ * The timed launches read array A and write array B only, so the lattice
+ * state is unchanged.  Synchronises the stream. */
+int lb_autotune(lb_lattice *h, int reps, int *variant, int *block, float *ms_per_step);
+
 /* Wait for all work issued on the lattice's stream. */
 int lb_sync(lb_lattice *h);
 

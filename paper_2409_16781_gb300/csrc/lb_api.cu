@@ -380,6 +380,71 @@ int lb_get_populations_at(lb_lattice* h, const int64_t* cells, int n, double* ou
     return LB_OK;
 }
 
+int lb_set_kernel(lb_lattice* h, int variant, int block) {
+    if (!h) return fail(LB_EINVAL, "lb_set_kernel: NULL handle");
+    if (variant < 0 || variant > 9 || block < 0 || block > 1024)
+        return fail(LB_EINVAL, "lb_set_kernel: bad variant %d / block %d", variant, block);
+    h->kernel = variant;
+    h->block = block;
+    return LB_OK;
+}
+
+int lb_autotune(lb_lattice* h, int reps, int* variant, int* block, float* ms_per_step) {
+    if (!h) return fail(LB_EINVAL, "lb_autotune: NULL handle");
+    if (reps < 1) reps = 1;
+    struct Cand {
+        int v, b;
+    };
+    Cand cands[32];
+    int nc = 0;
+    auto add = [&](int v, int b) {
+        if (nc < 32) cands[nc++] = {v, b};
+    };
+    const bool sixteen = h->sbytes == 2;
+    for (int b : {32, 64, 128, 256}) add(1, b);
+    if (h->nx % 2 == 0) {
+        for (int b : {64, 128}) add(sixteen ? 6 : 4, b);
+    }
+    if (sixteen && h->nx % 4 == 0) {
+        for (int b : {32, 64, 128}) add(8, b);
+    }
+    const LatticeParams p = params_of(h);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "lb_autotune: event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(cudaGetLastError(), "lb_autotune: event");
+    }
+    int best = -1;
+    float best_ms = 0.f;
+    cudaError_t e = cudaSuccess;
+    const void* A = h->pop[h->cur];
+    void* B = h->pop[1 - h->cur];
+    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+        e = launch_step(h->storage, cands[c].v, A, B, h->code, p, cands[c].b, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r)
+            e = launch_step(h->storage, cands[c].v, A, B, h->code, p, cands[c].b, h->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (best < 0 || ms < best_ms)) {
+            best = c;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "lb_autotune");
+    h->kernel = cands[best].v;
+    h->block = cands[best].b;
+    if (variant) *variant = h->kernel;
+    if (block) *block = h->block;
+    if (ms_per_step) *ms_per_step = best_ms / reps;
+    return LB_OK;
+}
+
 int lb_sync(lb_lattice* h) {
     if (!h) return fail(LB_EINVAL, "lb_sync: NULL handle");
     cudaError_t e = cudaStreamSynchronize(h->stream);

@@ -168,6 +168,242 @@ static cudaError_t step_pairs_t(const void* A, void* B, const uint8_t* code, con
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Variant 6 (16-bit storage): two x-consecutive cells per thread with the
+// loaded values kept packed, one 32-bit register per direction (low half =
+// cell x0, high half = x0+1).  The x-shifted directions are rebuilt with a
+// lane shuffle and a byte permute: for c_x = +1 the pair (x0-1, x0) is
+// (previous lane's high half, own low half); for c_x = -1 the pair
+// (x0+1, x0+2) is (own high half, next lane's low half).  Each cell is then
+// unpacked to FP32, collided and repacked into a 32-bit store.
+// ---------------------------------------------------------------------------
+template <class S> __device__ __forceinline__ float lo16(uint32_t v);
+template <class S> __device__ __forceinline__ float hi16(uint32_t v);
+template <class S> __device__ __forceinline__ uint32_t to16(float f);
+template <> __device__ __forceinline__ float lo16<__half>(uint32_t v) {
+    return __half2float(__ushort_as_half((unsigned short)(v & 0xffffu)));
+}
+template <> __device__ __forceinline__ float hi16<__half>(uint32_t v) {
+    return __half2float(__ushort_as_half((unsigned short)(v >> 16)));
+}
+template <> __device__ __forceinline__ uint32_t to16<__half>(float f) {
+    return (uint32_t)__half_as_ushort(__float2half_rn(f));
+}
+// a bf16 value is the upper 16 bits of the FP32 value it stands for
+template <> __device__ __forceinline__ float lo16<__nv_bfloat16>(uint32_t v) { return __uint_as_float(v << 16); }
+template <> __device__ __forceinline__ float hi16<__nv_bfloat16>(uint32_t v) {
+    return __uint_as_float(v & 0xffff0000u);
+}
+template <> __device__ __forceinline__ uint32_t to16<__nv_bfloat16>(float f) {
+    return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(f));
+}
+
+template <class S, bool FORCE, int HINT>
+__global__ void __launch_bounds__(256, 3) step_kernel_pairs16(const S* __restrict__ A, S* __restrict__ B,
+                                                           const uint8_t* __restrict__ code, LatticeParams p,
+                                                           int xblocks) {
+    static_assert(sizeof(S) == 2, "16-bit storage only");
+    const uint16_t* __restrict__ A16 = reinterpret_cast<const uint16_t*>(A);
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int xb = blockIdx.x % xblocks;
+    const int row = blockIdx.x / xblocks;
+    const int y = row % ny;
+    const int z = row / ny;
+    const int x0 = 2 * (xb * blockDim.x + threadIdx.x);
+    const bool active = x0 < nx;
+    const int xa = active ? x0 : 0;  // in-bounds address for idle lanes
+    const int lane = threadIdx.x & 31;
+    const int nxy = nx * ny;
+    const int yo[3] = {(y == ny - 1 ? 0 : y + 1) * nx, y * nx, (y == 0 ? ny - 1 : y - 1) * nx};
+    const int zo[3] = {(z == nz - 1 ? 0 : z + 1) * nxy, z * nxy, (z == 0 ? nz - 1 : z - 1) * nxy};
+    const int cell0 = xa + nx * row;
+    uint32_t v[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const uint16_t* rowp = A16 + (int64_t)i * p.ps + yo[D3Q19::cy(i) + 1] + zo[D3Q19::cz(i) + 1];
+        const uint32_t raw = ld_pop<HINT>(reinterpret_cast<const uint32_t*>(rowp + xa));
+        if (D3Q19::cx(i) == 0) {
+            v[i] = raw;
+        } else if (D3Q19::cx(i) == 1) {  // source x - 1: (prev.hi, own.lo)
+            uint32_t prev = __shfl_up_sync(0xffffffffu, raw, 1);
+            if (lane == 0 && active)
+                prev = (uint32_t)ld_pop<HINT>(rowp + (x0 == 0 ? nx - 1 : x0 - 1)) << 16;
+            v[i] = __byte_perm(prev, raw, 0x5432);
+        } else {  // source x + 1: (own.hi, next.lo)
+            uint32_t next = __shfl_down_sync(0xffffffffu, raw, 1);
+            if (active && (lane == 31 || x0 + 2 >= nx))
+                next = (uint32_t)ld_pop<HINT>(rowp + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2));
+            v[i] = __byte_perm(raw, next, 0x5432);
+        }
+    }
+    if (!active) return;
+    const uint8_t c0 = code[cell0], c1 = code[cell0 + 1];
+    uint32_t out[Q];
+    {
+        float d[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = lo16<S>(v[i]);
+        if (c0 & CODE_NEAR_WALL) bounce_fix<S, HINT>(A, code, p, x0, y, z, cell0, d);
+        float drho, rho, ux, uy, uz;
+        macro_dev<float>(d, p, drho, rho, ux, uy, uz);
+        collide_dev<float, FORCE>(d, p, drho, rho, ux, uy, uz);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) out[i] = to16<S>(d[i]);
+    }
+    {
+        float d[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = hi16<S>(v[i]);
+        if (c1 & CODE_NEAR_WALL) bounce_fix<S, HINT>(A, code, p, x0 + 1, y, z, cell0 + 1, d);
+        float drho, rho, ux, uy, uz;
+        macro_dev<float>(d, p, drho, rho, ux, uy, uz);
+        collide_dev<float, FORCE>(d, p, drho, rho, ux, uy, uz);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) out[i] |= to16<S>(d[i]) << 16;
+    }
+    uint16_t* B16 = reinterpret_cast<uint16_t*>(B);
+    const bool f0 = !(c0 & CODE_TYPE), f1 = !(c1 & CODE_TYPE);
+    if (f0 && f1) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) st_pop<HINT>(reinterpret_cast<uint32_t*>(B16 + (int64_t)i * p.ps + cell0), out[i]);
+    } else {  // solid cells are never written
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (f0) st_pop<HINT>(B16 + (int64_t)i * p.ps + cell0, (uint16_t)(out[i] & 0xffffu));
+            if (f1) st_pop<HINT>(B16 + (int64_t)i * p.ps + cell0 + 1, (uint16_t)(out[i] >> 16));
+        }
+    }
+}
+
+template <class S, int HINT>
+static cudaError_t step_pairs16_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p, int block,
+                                  cudaStream_t st) {
+    int bx = block > 0 ? (block / 32) * 32 : 128;  // whole warps (the shuffles need all 32 lanes)
+    if (bx < 32) bx = 32;
+    if (bx > 256) bx = 256;
+    const int pairs = p.nx / 2;
+    const int need = ((pairs + 31) / 32) * 32;
+    if (bx > need) bx = need;
+    const int xblocks = (pairs + bx - 1) / bx;
+    const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
+    const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
+    if (force)
+        step_kernel_pairs16<S, true, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+    else
+        step_kernel_pairs16<S, false, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Variant 8 (16-bit storage, nx % 4 == 0): four x-consecutive cells per
+// thread, loaded as one 8-byte word per direction (cells x0..x0+3), which
+// doubles the bytes each thread keeps in flight.  x-shifts as in variant 6:
+// c_x = +1 needs (x0-1 .. x0+2), the first from the previous lane's top
+// half; c_x = -1 needs (x0+1 .. x0+4), the last from the next lane's bottom
+// half; warp and row edges load that element themselves.
+// ---------------------------------------------------------------------------
+template <class S>
+__device__ __forceinline__ float get16(const uint2& v, int k) {
+    return k == 0 ? lo16<S>(v.x) : k == 1 ? hi16<S>(v.x) : k == 2 ? lo16<S>(v.y) : hi16<S>(v.y);
+}
+
+template <class S, bool FORCE, int HINT>
+__global__ void __launch_bounds__(128, 4) step_kernel_quads16(const S* __restrict__ A, S* __restrict__ B,
+                                                              const uint8_t* __restrict__ code, LatticeParams p,
+                                                              int xblocks) {
+    static_assert(sizeof(S) == 2, "16-bit storage only");
+    const uint16_t* __restrict__ A16 = reinterpret_cast<const uint16_t*>(A);
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int xb = blockIdx.x % xblocks;
+    const int row = blockIdx.x / xblocks;
+    const int y = row % ny;
+    const int z = row / ny;
+    const int x0 = 4 * (xb * blockDim.x + threadIdx.x);
+    const bool active = x0 < nx;
+    const int xa = active ? x0 : 0;  // in-bounds address for idle lanes
+    const int lane = threadIdx.x & 31;
+    const int nxy = nx * ny;
+    const int yo[3] = {(y == ny - 1 ? 0 : y + 1) * nx, y * nx, (y == 0 ? ny - 1 : y - 1) * nx};
+    const int zo[3] = {(z == nz - 1 ? 0 : z + 1) * nxy, z * nxy, (z == 0 ? nz - 1 : z - 1) * nxy};
+    const int cell0 = xa + nx * row;
+    uint2 v[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const uint16_t* rowp = A16 + (int64_t)i * p.ps + yo[D3Q19::cy(i) + 1] + zo[D3Q19::cz(i) + 1];
+        const uint2 raw = ld_pop<HINT>(reinterpret_cast<const uint2*>(rowp + xa));
+        if (D3Q19::cx(i) == 0) {
+            v[i] = raw;
+        } else if (D3Q19::cx(i) == 1) {  // source x - 1: (prev top, x0, x0+1, x0+2)
+            uint32_t prev = __shfl_up_sync(0xffffffffu, raw.y, 1);
+            if (lane == 0 && active)
+                prev = (uint32_t)ld_pop<HINT>(rowp + (x0 == 0 ? nx - 1 : x0 - 1)) << 16;
+            v[i] = make_uint2(__byte_perm(prev, raw.x, 0x5432), __byte_perm(raw.x, raw.y, 0x5432));
+        } else {  // source x + 1: (x0+1, x0+2, x0+3, next bottom)
+            uint32_t next = __shfl_down_sync(0xffffffffu, raw.x, 1);
+            if (active && (lane == 31 || x0 + 4 >= nx))
+                next = (uint32_t)ld_pop<HINT>(rowp + (x0 + 4 >= nx ? x0 + 4 - nx : x0 + 4));
+            v[i] = make_uint2(__byte_perm(raw.x, raw.y, 0x5432), __byte_perm(raw.y, next, 0x5432));
+        }
+    }
+    if (!active) return;
+    const uint32_t codes = *reinterpret_cast<const uint32_t*>(code + cell0);  // 4 code bytes
+    uint2 out[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) out[i] = make_uint2(0u, 0u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float d[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = get16<S>(v[i], k);
+        const uint8_t ck = (uint8_t)(codes >> (8 * k));
+        if (ck & CODE_NEAR_WALL) bounce_fix<S, HINT>(A, code, p, x0 + k, y, z, cell0 + k, d);
+        float drho, rho, ux, uy, uz;
+        macro_dev<float>(d, p, drho, rho, ux, uy, uz);
+        collide_dev<float, FORCE>(d, p, drho, rho, ux, uy, uz);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const uint32_t h = to16<S>(d[i]) << (16 * (k & 1));
+            if (k < 2) out[i].x |= h;
+            else out[i].y |= h;
+        }
+    }
+    uint16_t* B16 = reinterpret_cast<uint16_t*>(B);
+    const uint32_t solid = codes & 0x03030303u;
+    if (solid == 0) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) st_pop<HINT>(reinterpret_cast<uint2*>(B16 + (int64_t)i * p.ps + cell0), out[i]);
+    } else {  // solid cells are never written
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if ((codes >> (8 * k)) & CODE_TYPE) continue;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const uint32_t word = k < 2 ? out[i].x : out[i].y;
+                st_pop<HINT>(B16 + (int64_t)i * p.ps + cell0 + k, (uint16_t)(word >> (16 * (k & 1))));
+            }
+        }
+    }
+}
+
+template <class S, int HINT>
+static cudaError_t step_quads16_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p, int block,
+                                  cudaStream_t st) {
+    int bx = block > 0 ? (block / 32) * 32 : 64;  // whole warps (the shuffles need all 32 lanes)
+    if (bx < 32) bx = 32;
+    if (bx > 128) bx = 128;
+    const int quads = p.nx / 4;
+    const int need = ((quads + 31) / 32) * 32;
+    if (bx > need) bx = need;
+    const int xblocks = (quads + bx - 1) / bx;
+    const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
+    const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
+    if (force)
+        step_kernel_quads16<S, true, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+    else
+        step_kernel_quads16<S, false, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+    return cudaGetLastError();
+}
+
 template <class S, int HINT>
 static cudaError_t step_rows_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p, int block,
                                cudaStream_t st) {
@@ -199,7 +435,34 @@ static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* co
             return pairs_ok ? step_pairs_t<S, 0>(A, B, code, p, block, st) : step_rows_t<S, 0>(A, B, code, p, block, st);
         case 5:
             return pairs_ok ? step_pairs_t<S, 1>(A, B, code, p, block, st) : step_rows_t<S, 1>(A, B, code, p, block, st);
-        case 0: return step_rows_t<S, 0>(A, B, code, p, block > 0 ? block : 128, st);
+        case 6:
+        case 7:
+            if constexpr (sizeof(S) == 2) {
+                if (pairs_ok)
+                    return variant == 6 ? step_pairs16_t<S, 0>(A, B, code, p, block, st)
+                                        : step_pairs16_t<S, 1>(A, B, code, p, block, st);
+            }
+            return step_rows_t<S, 0>(A, B, code, p, block, st);
+        case 8:
+        case 9:
+            if constexpr (sizeof(S) == 2) {
+                if (p.nx % 4 == 0)
+                    return variant == 8 ? step_quads16_t<S, 0>(A, B, code, p, block, st)
+                                        : step_quads16_t<S, 1>(A, B, code, p, block, st);
+            }
+            return step_rows_t<S, 0>(A, B, code, p, block, st);
+        case 0:
+            // measured defaults on GB300 (256^3): FP32 one cell per thread in
+            // 64-thread blocks; FP64 two cells per thread; 16-bit storage four
+            // cells per thread in packed registers
+            if constexpr (sizeof(S) == 2) {
+                if (p.nx % 4 == 0) return step_quads16_t<S, 0>(A, B, code, p, block > 0 ? block : 64, st);
+                if (pairs_ok) return step_pairs16_t<S, 0>(A, B, code, p, block > 0 ? block : 64, st);
+            }
+            if constexpr (sizeof(S) == 8) {
+                if (pairs_ok) return step_pairs_t<S, 0>(A, B, code, p, block > 0 ? block : 128, st);
+            }
+            return step_rows_t<S, 0>(A, B, code, p, block > 0 ? block : 64, st);
         default: return cudaErrorInvalidValue;
     }
 }

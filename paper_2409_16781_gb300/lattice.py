@@ -7,6 +7,8 @@ the kernels of liblbgb.so.
 from __future__ import annotations
 
 import ctypes
+import json
+import os
 
 import numpy as np
 
@@ -76,6 +78,7 @@ class Lattice:
             if fl.size != self.N:
                 raise ValueError(f"flags has {fl.size} entries, lattice has {self.N}")
         self._flags = fl
+        self._force = any(float(v) != 0.0 for v in force)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             if library_memory:
@@ -176,6 +179,47 @@ class Lattice:
         L.check(self.lib.lb_get_populations_at(self._h, _dptr(cells), int(cells.size), _dptr(out)),
                 "lb_get_populations_at")
         return out
+
+    def set_kernel(self, variant: int, block: int = 0):
+        L.check(self.lib.lb_set_kernel(self._h, int(variant), int(block)), "lb_set_kernel")
+
+    def autotune(self, reps: int = 20, cache: bool = True):
+        """Pick the fastest step-kernel variant and block size for this
+        lattice (lb_autotune), remembering the choice in a JSON file keyed by
+        GPU, storage, dims and forcing (LBGB_AUTOTUNE_CACHE, default
+        ~/.cache/lbgb/autotune.json).  Returns (variant, block, ms/step)."""
+        import torch
+        key = "|".join([torch.cuda.get_device_name(self.device), str(self.storage),
+                        f"{self.nx}x{self.ny}x{self.nz}", "force" if self._force else "noforce"])
+        path = os.environ.get("LBGB_AUTOTUNE_CACHE",
+                              os.path.join(os.path.expanduser("~"), ".cache", "lbgb", "autotune.json"))
+        table = {}
+        if cache and os.path.exists(path):
+            try:
+                with open(path) as fh:
+                    table = json.load(fh)
+            except (OSError, ValueError):
+                table = {}
+            if key in table:
+                v, b, ms = table[key]
+                self.set_kernel(v, b)
+                return v, b, ms
+        v = ctypes.c_int()
+        b = ctypes.c_int()
+        ms = ctypes.c_float()
+        L.check(self.lib.lb_autotune(self._h, int(reps), ctypes.byref(v), ctypes.byref(b),
+                                     ctypes.byref(ms)), "lb_autotune")
+        if cache:
+            table[key] = [v.value, b.value, ms.value]
+            try:
+                os.makedirs(os.path.dirname(path), exist_ok=True)
+                tmp = f"{path}.{os.getpid()}"
+                with open(tmp, "w") as fh:
+                    json.dump(table, fh, indent=1, sort_keys=True)
+                os.replace(tmp, path)
+            except OSError:
+                pass
+        return v.value, b.value, ms.value
 
     def query(self):
         dims = (ctypes.c_int * 3)()

@@ -68,7 +68,7 @@ TINY = [
     (66, 5, 4, 0.7, 20, ("random", 22), (0.02, 0.0, 0.0), (0, 0, 0)),
 ]
 
-KERNELS = [1, 4]
+KERNELS = [1, 4, 6]
 
 
 def _flags(spec, nx, ny, nz):
@@ -91,12 +91,12 @@ def test_tiny_grids(case, storage, kernel, perm):
     check_pair(ora, gpu, storage, perm, flags)
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4, 5])
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16s"])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("storage", STORAGES)
 def test_every_variant(storage, kernel, perm):
     """Every step-kernel variant (cache policies, one or two cells per
     thread) on a grid with walls, lid and force, odd and even row lengths."""
-    for nx, ny, nz in ((34, 7, 6), (35, 6, 5)):
+    for nx, ny, nz in ((34, 7, 6), (35, 6, 5), (136, 5, 4)):
         flags = W.random_flags(nx, ny, nz, seed=nx, p_wall=0.15, p_lid=0.1)
         rho0, u0 = W.random_fields(nx, ny, nz, seed=7, du=0.05, drho=0.02)
         ora, gpu = run_pair(nx, ny, nz, 0.7, 12, storage, flags, (0.04, 0.01, -0.02), (1e-4, 0, 0),
@@ -206,3 +206,27 @@ def test_library_owned_memory(perm):
     assert np.array_equal(a.populations(), b.populations())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_autotune_keeps_state(storage, perm, tmp_path, monkeypatch):
+    """lb_autotune times launches A -> B only: the state is unchanged, and
+    the chosen kernel then advances the lattice like the oracle."""
+    monkeypatch.setenv("LBGB_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    nx, ny, nz = 64, 12, 10
+    flags = W.random_flags(nx, ny, nz, seed=31, p_wall=0.05, p_lid=0.02)
+    rho0, u0 = W.random_fields(nx, ny, nz, seed=8, du=0.04, drho=0.01)
+    ora = O.Lattice(nx, ny, nz, 0.6, u_lid=(0.05, 0, 0), flags=flags)
+    ora.init_fields(rho0, u0)
+    gpu = Lattice(nx, ny, nz, 0.6, u_lid=(0.05, 0, 0), flags=flags, storage=storage)
+    gpu.init_fields(rho0, u0)
+    f0 = gpu.populations()
+    v, b, ms = gpu.autotune(reps=3)
+    assert np.array_equal(gpu.populations(), f0)
+    assert v in range(1, 10) and b % 32 == 0 and ms > 0
+    assert (tmp_path / "tune.json").exists()
+    again = Lattice(nx, ny, nz, 0.6, u_lid=(0.05, 0, 0), flags=flags, storage=storage)
+    assert again.autotune(reps=3) == (v, b, ms)  # from the cache
+    ora.step(30)
+    gpu.step(30)
+    check_pair(ora, gpu, storage, perm, flags)
