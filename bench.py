@@ -37,6 +37,8 @@ if ROOT not in sys.path:
 METRIC = "D3Q19 MLUPS & fraction of HBM roofline; batched-serve p50/p99 vs plain FP32 launches"
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
 FALLBACK_HBM_GBS = 6800.0
+# the files that make up the step kernel (hashed to tie ncu figures to it)
+STEP_SOURCES = ("lb_common.cuh", "lb_kernels.cuh", "lb_step.cu")
 
 
 def bytes_per_update(storage: str) -> int:
@@ -191,10 +193,9 @@ def kernel_source_hash() -> str:
     reported while it matches the kernels being timed."""
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2409_16781_gb300", "csrc")
-    for name in sorted(os.listdir(cs)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(cs, name), "rb") as fh:
-                h.update(name.encode() + b"\0" + fh.read())
+    for name in STEP_SOURCES:
+        with open(os.path.join(cs, name), "rb") as fh:
+            h.update(name.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
 
 
