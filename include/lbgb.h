@@ -161,6 +161,36 @@ int lb_set_kernel(lb_lattice *h, int variant, int block);
  * state is unchanged.  Synchronises the stream. */
 int lb_autotune(lb_lattice *h, int reps, int *variant, int *block, float *ms_per_step);
 
+/* Totals without any allocation (the paper has no counterpart: it is a
+ * service for callers that cannot allocate device memory -- code running
+ * inside another framework's memory pool or a fixed memory budget, or a
+ * real-time loop where an allocation may block or fail -- and that hold the
+ * populations in their own buffers).  Same result as lb_totals.
+ *   populations  device, 19 planes of plane_stride >= N elements of the
+ *                storage type, each value the deviation f_i - w_i, library
+ *                velocity order (the layout lb_create uses);
+ *   flags        device, N bytes, LB_FLUID/LB_WALL/LB_LID (the two low bits
+ *                are read);
+ *   force, u_lid host, 3 doubles each or NULL (= 0);
+ *   stream       cudaStream_t or NULL; the call synchronises it;
+ *   out          host, 5 doubles: mass, momentum x/y/z, count of fluid
+ *                cells with non-finite or non-positive density.
+ * The reduction's scratch is a static device array of
+ * LB_STATIC_MAX_BLOCKS * 6 + 8 doubles (about 58 KB) that every GPU loading
+ * the library holds until exit; the kernel strides over the lattice with at
+ * most LB_STATIC_MAX_BLOCKS blocks, so any lattice below 2^31 cells fits and
+ * larger ones are rejected (LB_EINVAL).  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  The array is
+ * shared by all calls and keeps the last call's values: calls that overlap
+ * on the GPU race on it and must be serialised by the caller.  Calls no
+ * cudaMalloc or cudaFree.  Returns LB_OK, LB_EINVAL, LB_ECUDA, or
+ * LB_EDIVERGED (after filling out). */
+#define LB_STATIC_MAX_BLOCKS 1216
+int lb_totals_static(const void *populations, int64_t plane_stride, const uint8_t *flags,
+                     int nx, int ny, int nz, int storage, const double *force,
+                     const double *u_lid, void *stream, double *out);
+
 /* Wait for all work issued on the lattice's stream. */
 int lb_sync(lb_lattice *h);
 

@@ -60,6 +60,7 @@ SIGNATURES = {
     "lb_get_populations_at": (_I, [_P, _P, _I, _P]),
     "lb_set_kernel": (_I, [_P, _I, _I]),
     "lb_autotune": (_I, [_P, _I, _P, _P, _P]),
+    "lb_totals_static": (_I, [_P, _I64, _P, _I, _I, _I, _I, _P, _P, _P, _P]),
     "lb_sync": (_I, [_P]),
     "lb_query": (_I, [_P, _P, _P, _P]),
     "lb_destroy": (_I, [_P]),
