@@ -149,7 +149,10 @@ int lb_get_populations_at(lb_lattice *h, const int64_t *cells, int n, double *ou
  * 2, 3 as 1 with streaming / L2-only cache policies; 4, 5 two cells per
  * thread (even nx); 6, 7 two cells per thread, packed 16-bit registers
  * (16-bit storage, even nx); 8, 9 four cells per thread, packed 16-bit
- * (16-bit storage, nx % 4 == 0).  A variant that does not apply to the
+ * (16-bit storage, nx % 4 == 0); 10, 11 TMA bulk-copy pipeline through
+ * shared memory, four / two cells per thread (16-bit storage, nx % 16 == 0;
+ * block size fixed).  A variant that
+ * does not apply to the
  * lattice runs variant 1.  block = threads per block (0 = default; rounded
  * down to whole warps). */
 int lb_set_kernel(lb_lattice *h, int variant, int block);
@@ -191,7 +194,9 @@ int lb_totals_static(const void *populations, int64_t plane_stride, const uint8_
                      int nx, int ny, int nz, int storage, const double *force,
                      const double *u_lid, void *stream, double *out);
 
-/* Wait for all work issued on the lattice's stream. */
+/* Wait for all work issued on the lattice's stream.  Returns LB_ETIMEOUT
+ * (and clears the condition) if a kernel's bounded wait on an asynchronous
+ * copy gave up since the last check. */
 int lb_sync(lb_lattice *h);
 
 /* Query: dims[3], storage, steps taken since create. */

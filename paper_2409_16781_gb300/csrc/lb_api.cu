@@ -26,6 +26,7 @@ struct lb_lattice {
     uint8_t* code;
     double* partials;
     double* tot_out;
+    int* err;  // device error word set by kernels whose bounded waits gave up
     void* staging;
     size_t staging_bytes;
     cudaStream_t stream;
@@ -109,12 +110,28 @@ LatticeParams params_of(const lb_lattice* h) {
         p.g[a] = h->g[a];
         p.ulid[a] = h->ulid[a];
     }
+    p.err = h->err;
     return p;
 }
 
 int64_t chunk_cells(const lb_lattice* h, size_t bytes_per_cell) {
     int64_t c = (int64_t)(h->staging_bytes / bytes_per_cell);
     return c < 1 ? 1 : c;
+}
+
+// Read (and clear) the device error word after the stream has drained.
+int check_device_error(lb_lattice* h, const char* what) {
+    int err = 0;
+    cudaError_t e = cudaMemcpyAsync(&err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (err != 0) {
+        const int zero = 0;
+        e = cudaMemcpyAsync(h->err, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        return fail(LB_ETIMEOUT, "%s: a bounded device-side wait gave up (error word 0x%x)", what, err);
+    }
+    return LB_OK;
 }
 
 int create_common(lb_lattice** out, int nx, int ny, int nz, double tau, const double* u_lid, const uint8_t* flags,
@@ -175,6 +192,7 @@ int create_common(lb_lattice** out, int nx, int ny, int nz, double tau, const do
     h->code = (uint8_t*)(b + L.code_off);
     h->partials = (double*)(b + L.part_off);
     h->tot_out = (double*)(b + L.tot_off);
+    h->err = (int*)(b + L.tot_off + 128);
     h->staging = b + L.stage_off;
     h->staging_bytes = L.stage_bytes;
     h->steps = 0;
@@ -191,6 +209,7 @@ int create_common(lb_lattice** out, int nx, int ny, int nz, double tau, const do
     } else {
         e = cudaMemsetAsync(h->code, 0, (size_t)L.N, h->stream);
     }
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
     if (e != cudaSuccess) rc = cuda_fail(e, "lb_create: flags");
     if (rc == LB_OK) {
         e = launch_init(h->storage, h->pop[0], h->pop[1], h->ps, nullptr, nullptr, 0, 0, h->N, h->stream);
@@ -316,6 +335,8 @@ int lb_totals(lb_lattice* h, double* mass, double* mom) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->tot_out, sizeof out, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "lb_totals");
+    const int rc = check_device_error(h, "lb_totals");
+    if (rc != LB_OK) return rc;
     if (mass) *mass = out[0];
     if (mom)
         for (int a = 0; a < 3; ++a) mom[a] = out[1 + a];
@@ -382,7 +403,7 @@ int lb_get_populations_at(lb_lattice* h, const int64_t* cells, int n, double* ou
 
 int lb_set_kernel(lb_lattice* h, int variant, int block) {
     if (!h) return fail(LB_EINVAL, "lb_set_kernel: NULL handle");
-    if (variant < 0 || variant > 9 || block < 0 || block > 1024)
+    if (variant < 0 || variant > 11 || block < 0 || block > 1024)
         return fail(LB_EINVAL, "lb_set_kernel: bad variant %d / block %d", variant, block);
     h->kernel = variant;
     h->block = block;
@@ -407,6 +428,10 @@ int lb_autotune(lb_lattice* h, int reps, int* variant, int* block, float* ms_per
     }
     if (sixteen && h->nx % 4 == 0) {
         for (int b : {32, 64, 128}) add(8, b);
+    }
+    if (sixteen && h->nx % 16 == 0) {
+        add(10, 0);
+        add(11, 0);
     }
     const LatticeParams p = params_of(h);
     cudaEvent_t e0, e1;
@@ -448,7 +473,8 @@ int lb_autotune(lb_lattice* h, int reps, int* variant, int* block, float* ms_per
 int lb_sync(lb_lattice* h) {
     if (!h) return fail(LB_EINVAL, "lb_sync: NULL handle");
     cudaError_t e = cudaStreamSynchronize(h->stream);
-    return e == cudaSuccess ? LB_OK : cuda_fail(e, "lb_sync");
+    if (e != cudaSuccess) return cuda_fail(e, "lb_sync");
+    return check_device_error(h, "lb_sync");
 }
 
 int lb_query(lb_lattice* h, int* dims, int* storage, int64_t* steps) {

@@ -29,6 +29,17 @@ struct D3Q19 {
         constexpr int t[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
         return t[i];
     }
+    // The same components for a run-time index, from 2-bit fields (c + 1) of
+    // 64-bit constants (no table in local memory).
+    __host__ __device__ static constexpr uint64_t pack_(int a) {
+        uint64_t k = 0;
+        for (int i = 0; i < Q; ++i)
+            k |= (uint64_t)((a == 0 ? cx(i) : a == 1 ? cy(i) : cz(i)) + 1) << (2 * i);
+        return k;
+    }
+    __host__ __device__ static int cx_rt(int i) { return (int)((pack_(0) >> (2 * i)) & 3u) - 1; }
+    __host__ __device__ static int cy_rt(int i) { return (int)((pack_(1) >> (2 * i)) & 3u) - 1; }
+    __host__ __device__ static int cz_rt(int i) { return (int)((pack_(2) >> (2 * i)) & 3u) - 1; }
     __host__ __device__ static constexpr int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
     __host__ __device__ static constexpr double w(int i) {
         return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
@@ -79,6 +90,10 @@ struct LatticeParams {
     double omega;     // 1/tau
     double g[3];      // body force per unit mass
     double ulid[3];   // lid velocity
+    int* err;         // device error word (bounded waits that gave up), or nullptr
 };
+
+// Error bits a kernel may set in LatticeParams::err.
+constexpr int ERR_WAIT_TIMEOUT = 1;
 
 }  // namespace lbgb

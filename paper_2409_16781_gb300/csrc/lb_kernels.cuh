@@ -120,6 +120,11 @@ __device__ __forceinline__ void moment_sums(const M (&d)[Q], M& drho, M& jx, M& 
     drho = s;
 }
 
+// 1/rho: IEEE division in FP64; in FP32 the approximate reciprocal (about
+// 2 ulp) -- far below the FP32 tolerance and several instructions shorter.
+__device__ __forceinline__ double recip(double r) { return 1.0 / r; }
+__device__ __forceinline__ float recip(float r) { return __fdividef(1.0f, r); }
+
 // Density and half-force-shifted velocity u = j/rho + g/2 from deviations.
 template <class M>
 __device__ __forceinline__ void macro_dev(const M (&d)[Q], const LatticeParams& p, M& drho, M& rho,
@@ -127,7 +132,7 @@ __device__ __forceinline__ void macro_dev(const M (&d)[Q], const LatticeParams& 
     M jx, jy, jz;
     moment_sums<M>(d, drho, jx, jy, jz);
     rho = M(1) + drho;
-    const M inv = M(1) / rho;
+    const M inv = recip(rho);
     ux = jx * inv + M(0.5) * (M)p.g[0];
     uy = jy * inv + M(0.5) * (M)p.g[1];
     uz = jz * inv + M(0.5) * (M)p.g[2];
@@ -155,16 +160,32 @@ __device__ __forceinline__ void collide_dev(M (&d)[Q], const LatticeParams& p, M
         uF = ux * Fx + uy * Fy + uz * Fz;
         pref = M(1) - M(0.5) * om;
     }
+    // per weight class W: even = aW cu^2 + bW (+ force), odd = cW cu (+ force)
+    //   aW = 4.5 omega W rho, bW = omega W (drho - 1.5 rho uu), cW = 3 omega W rho
+    const M wa = (M)D3Q19::w(1), wb = (M)D3Q19::w(7);
+    const M orho = om * rho;
+    const M base = om * (drho - rho * uu15);
+    const M a1 = M(4.5) * wa * orho, b1 = wa * base, c1 = M(3) * wa * orho;
+    const M a2 = M(4.5) * wb * orho, b2 = wb * base, c2 = M(3) * wb * orho;
+    M fa1 = 0, fb1 = 0, fc1 = 0, fa2 = 0, fb2 = 0, fc2 = 0;
+    if (FORCE) {  // Guo: even (1-omega/2) W (9 cu cF - 3 uF), odd (1-omega/2) 3 W cF
+        fa1 = M(9) * pref * wa;
+        fb1 = M(-3) * pref * wa * uF;
+        fc1 = M(3) * pref * wa;
+        fa2 = M(9) * pref * wb;
+        fb2 = M(-3) * pref * wb * uF;
+        fc2 = M(3) * pref * wb;
+    }
     {
         const M w0 = (M)D3Q19::w(0);
-        M e = om * (w0 * (drho - rho * uu15));
+        M e = w0 * base;
         if (FORCE) e += pref * w0 * (M(-3) * uF);
         d[0] = omc * d[0] + e;
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const int i = 2 * k + 1;
-        const M w = (M)D3Q19::w(i);
+        const bool axis = i <= 6;
         M cu = 0, cF = 0;
         if (D3Q19::cx(i) == 1) { cu += ux; cF += Fx; }
         if (D3Q19::cx(i) == -1) { cu -= ux; cF -= Fx; }
@@ -172,11 +193,11 @@ __device__ __forceinline__ void collide_dev(M (&d)[Q], const LatticeParams& p, M
         if (D3Q19::cy(i) == -1) { cu -= uy; cF -= Fy; }
         if (D3Q19::cz(i) == 1) { cu += uz; cF += Fz; }
         if (D3Q19::cz(i) == -1) { cu -= uz; cF -= Fz; }
-        M even = om * (w * (drho + rho * (M(4.5) * cu * cu - uu15)));
-        M odd = om * (M(3) * w * rho * cu);
+        M even = (axis ? a1 : a2) * (cu * cu) + (axis ? b1 : b2);
+        M odd = (axis ? c1 : c2) * cu;
         if (FORCE) {
-            even += pref * w * (M(9) * cu * cF - M(3) * uF);
-            odd += pref * (M(3) * w) * cF;
+            even += (axis ? fa1 : fa2) * (cu * cF) + (axis ? fb1 : fb2);
+            odd += (axis ? fc1 : fc2) * cF;
         }
         d[i] = omc * d[i] + (even + odd);
         d[i + 1] = omc * d[i + 1] + (even - odd);

@@ -13,6 +13,8 @@
 // x-shifted ones are offset by one element and pick up one extra sector,
 // served from L1/L2).  Interior cells read only their own code byte; cells
 // next to a wall read the 18 neighbour codes (cached) for bounce-back.
+#include <type_traits>
+
 #include "lb_internal.h"
 #include "lb_kernels.cuh"
 
@@ -406,6 +408,360 @@ static cudaError_t step_quads16_t(const void* A, void* B, const uint8_t* code, c
 
 template <class S, int HINT>
 static cudaError_t step_rows_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p, int block,
+                               cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Variant 10 (16-bit storage, nx % 16 == 0): TMA bulk-copy pipeline.
+// A tile is R rows x TX cells (R * TX = 512).  One producer warp copies, for
+// every row of the tile and every direction i, the source run of plane i at
+// row (y - c_y, z - c_z), x in [x0, x0 + TX), into shared memory with
+// cp.async.bulk, plus a 16-byte halo before it (c_x = +1) or after it
+// (c_x = -1), wrapped periodically, and the tile's code bytes; the copies
+// complete on the stage's "full" mbarrier.  Four consumer warps wait on it,
+// compute four cells per thread from shared memory (x-shifts are aligned
+// 4- and 8-byte loads plus byte permutes) and store to B directly, then
+// release the stage on its "empty" mbarrier.  Bytes in flight live in the
+// STAGES-deep shared-memory ring, not in registers.  Every wait is bounded
+// (iteration cap and a 2 s %globaltimer deadline); a wait that gives up sets
+// ERR_WAIT_TIMEOUT in p.err and the block stops, after the producer has
+// waited (again bounded) for the copies it issued.
+// ---------------------------------------------------------------------------
+constexpr int TMA_STAGES = 4;
+constexpr int TMA_CONSUMER_WARPS = 4;
+constexpr int TMA_THREADS = 32 * (1 + TMA_CONSUMER_WARPS);
+constexpr int TMA_HALO = 8;  // 16 bytes of 16-bit values
+// cells per tile with G cells per consumer thread
+__host__ __device__ constexpr int tma_tile_cells(int G) { return G * 32 * TMA_CONSUMER_WARPS; }
+// largest stage ring: TX = 16 -> R = tile/16 rows of 19 * (16 + 16) * 2 + 16 bytes
+__host__ __device__ constexpr int tma_max_smem(int G) {
+    return TMA_STAGES * (tma_tile_cells(G) / 16) * (19 * (16 + 2 * TMA_HALO) * 2 + 16);
+}
+
+struct TmaGeom {
+    int TX;          // tile width in cells (divides nx, multiple of 16)
+    int R;           // rows per tile
+    int xchunks;     // nx / TX
+    int nrows;       // ny * nz
+    int64_t ntiles;  // xchunks * ceil(nrows / R)
+    int rb;          // bytes of one (row, direction) buffer: (TX + 2 halo) * 2
+    int row_bytes;   // 19 * rb + TX (codes)
+    int stage_bytes; // R * row_bytes
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the phase of parity `parity` to complete.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (int it = 0; it < (1 << 24); ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 63) == 63 && global_ns() - t0 > 2000000000ull) return false;
+    }
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+template <class S, bool FORCE, int G>
+__global__ void __launch_bounds__(TMA_THREADS, G == 4 ? 2 : 4) step_kernel_tma16(const S* __restrict__ A, S* __restrict__ B,
+                                                                 const uint8_t* __restrict__ code, LatticeParams p,
+                                                                 TmaGeom g) {
+    static_assert(sizeof(S) == 2, "16-bit storage only");
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t full_bar[TMA_STAGES];
+    __shared__ __align__(8) uint64_t empty_bar[TMA_STAGES];
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TMA_STAGES; ++s) {
+            mbar_init(smem_addr(&full_bar[s]), 1);
+            mbar_init(smem_addr(&empty_bar[s]), TMA_CONSUMER_WARPS);
+        }
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const uint16_t* A16 = reinterpret_cast<const uint16_t*>(A);
+
+    if (warp == 0) {
+        // ------------------------------ producer ------------------------------
+        int64_t k = 0;
+        for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x, ++k) {
+            const int s = (int)(k % TMA_STAGES);
+            const uint32_t n = (uint32_t)(k / TMA_STAGES);
+            bool ok = true;
+            if (lane == 0) {
+                if (k >= TMA_STAGES) ok = mbar_wait(smem_addr(&empty_bar[s]), (n - 1) & 1);
+                if (ok && *(volatile int*)&abort_flag) ok = false;
+            }
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) {
+                if (lane == 0) {
+                    atomicOr(p.err, ERR_WAIT_TIMEOUT);
+                    *(volatile int*)&abort_flag = 1;
+                }
+                break;
+            }
+            const int xc = (int)(t % g.xchunks);
+            const int row0 = (int)(t / g.xchunks) * g.R;
+            const int rows = min(g.R, g.nrows - row0);
+            const int x0 = xc * g.TX;
+            const uint32_t fb = smem_addr(&full_bar[s]);
+            if (lane == 0) mbar_expect_tx(fb, (uint32_t)rows * (19u * g.TX * 2u + 10u * 16u + (uint32_t)g.TX));
+            __syncwarp();
+            const uint32_t stage = smem_addr(smem) + (uint32_t)s * g.stage_bytes;
+            for (int idx = lane; idx < rows * 20; idx += 32) {
+                const int r = idx / 20, i = idx % 20;
+                const int row = row0 + r;
+                const uint32_t rbase = stage + (uint32_t)r * g.row_bytes;
+                if (i == 19) {  // the tile's code bytes
+                    bulk_g2s(rbase + 19u * g.rb, code + (int64_t)row * nx + x0, (uint32_t)g.TX, fb);
+                    continue;
+                }
+                const int y = row % ny, z = row / ny;
+                int sy = y - D3Q19::cy_rt(i), sz = z - D3Q19::cz_rt(i);
+                sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+                sz = sz < 0 ? sz + nz : (sz >= nz ? sz - nz : sz);
+                const uint16_t* srow = A16 + (int64_t)i * p.ps + ((int64_t)sz * ny + sy) * nx;
+                const uint32_t buf = rbase + (uint32_t)i * g.rb;
+                bulk_g2s(buf + 2u * TMA_HALO, srow + x0, 2u * g.TX, fb);
+                const int cxi = D3Q19::cx_rt(i);
+                if (cxi == 1)  // needs x0 - 1: halo before, wrapping at x = 0
+                    bulk_g2s(buf, srow + (x0 == 0 ? nx - TMA_HALO : x0 - TMA_HALO), 16u, fb);
+                else if (cxi == -1)  // needs x0 + TX: halo after, wrapping at x = nx
+                    bulk_g2s(buf + 2u * (TMA_HALO + g.TX), srow + (x0 + g.TX == nx ? 0 : x0 + g.TX), 16u, fb);
+            }
+        }
+        // do not leave while copies into this block's shared memory are in flight
+        if (lane == 0) {
+            const int64_t used = k < TMA_STAGES ? k : TMA_STAGES;
+            for (int64_t q = k - used; q < k; ++q) {
+                const int s = (int)(q % TMA_STAGES);
+                if (!mbar_wait(smem_addr(&full_bar[s]), (uint32_t)(q / TMA_STAGES) & 1)) atomicOr(p.err, ERR_WAIT_TIMEOUT);
+            }
+        }
+        return;
+    }
+
+    // -------------------------------- consumers --------------------------------
+    const int ct = (warp - 1) * 32 + lane;  // 0 .. 127
+    const int groups_per_row = g.TX / G;
+    const int r = ct / groups_per_row, j = ct % groups_per_row;
+    using W = typename std::conditional<G == 4, uint2, uint32_t>::type;  // G packed 16-bit values
+    int64_t k = 0;
+    for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x, ++k) {
+        const int s = (int)(k % TMA_STAGES);
+        const uint32_t n = (uint32_t)(k / TMA_STAGES);
+        bool ok = true;
+        if (lane == 0) {
+            ok = mbar_wait(smem_addr(&full_bar[s]), n & 1);
+            if (ok && *(volatile int*)&abort_flag) ok = false;
+        }
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (!ok) {
+            if (lane == 0) {
+                atomicOr(p.err, ERR_WAIT_TIMEOUT);
+                *(volatile int*)&abort_flag = 1;
+            }
+            break;
+        }
+        const int xc = (int)(t % g.xchunks);
+        const int row0 = (int)(t / g.xchunks) * g.R;
+        const int rows = min(g.R, g.nrows - row0);
+        const bool mine = r < rows;
+        // a thread without a row in this (last, partial) tile reads row 0 and discards it
+        const uint8_t* rb8 = smem + (size_t)s * g.stage_bytes + (size_t)(mine ? r : 0) * g.row_bytes;
+        W v[Q];
+        uint32_t codes;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const uint8_t* b = rb8 + i * g.rb + 2 * (TMA_HALO + G * j);
+            if constexpr (G == 4) {
+                const uint2 q = *reinterpret_cast<const uint2*>(b);
+                if (D3Q19::cx(i) == 0) {
+                    v[i] = q;
+                } else if (D3Q19::cx(i) == 1) {  // (x-1, x, x+1, x+2)
+                    const uint32_t pr = *reinterpret_cast<const uint32_t*>(b - 4);
+                    v[i] = make_uint2(__byte_perm(pr, q.x, 0x5432), __byte_perm(q.x, q.y, 0x5432));
+                } else {  // (x+1, x+2, x+3, x+4)
+                    const uint32_t nw = *reinterpret_cast<const uint32_t*>(b + 8);
+                    v[i] = make_uint2(__byte_perm(q.x, q.y, 0x5432), __byte_perm(q.y, nw, 0x5432));
+                }
+            } else {
+                const uint32_t q = *reinterpret_cast<const uint32_t*>(b);
+                if (D3Q19::cx(i) == 0) {
+                    v[i] = q;
+                } else if (D3Q19::cx(i) == 1) {  // (x-1, x)
+                    v[i] = __byte_perm(*reinterpret_cast<const uint32_t*>(b - 4), q, 0x5432);
+                } else {  // (x+1, x+2)
+                    v[i] = __byte_perm(q, *reinterpret_cast<const uint32_t*>(b + 4), 0x5432);
+                }
+            }
+        }
+        if constexpr (G == 4)
+            codes = *reinterpret_cast<const uint32_t*>(rb8 + 19 * g.rb + 4 * j);
+        else
+            codes = *reinterpret_cast<const uint16_t*>(rb8 + 19 * g.rb + 2 * j);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&empty_bar[s]));  // this warp's shared-memory reads are done
+        if (!mine) continue;
+        const int row = row0 + r;
+        const int y = row % ny, z = row / ny;
+        const int xq = xc * g.TX + G * j;
+        const int cell0 = xq + nx * row;
+        W out[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if constexpr (G == 4) out[i] = make_uint2(0u, 0u);
+            else out[i] = 0u;
+        }
+#pragma unroll
+        for (int kk = 0; kk < G; ++kk) {
+            float d[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                if constexpr (G == 4) d[i] = get16<S>(v[i], kk);
+                else d[i] = kk == 0 ? lo16<S>(v[i]) : hi16<S>(v[i]);
+            }
+            const uint8_t ck = (uint8_t)(codes >> (8 * kk));
+            if (ck & CODE_NEAR_WALL) bounce_fix<S, 0>(A, code, p, xq + kk, y, z, cell0 + kk, d);
+            float drho, rho, ux, uy, uz;
+            macro_dev<float>(d, p, drho, rho, ux, uy, uz);
+            collide_dev<float, FORCE>(d, p, drho, rho, ux, uy, uz);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const uint32_t h = to16<S>(d[i]) << (16 * (kk & 1));
+                if constexpr (G == 4) {
+                    if (kk < 2) out[i].x |= h;
+                    else out[i].y |= h;
+                } else {
+                    out[i] |= h;
+                }
+            }
+        }
+        uint16_t* B16 = reinterpret_cast<uint16_t*>(B);
+        const uint32_t solid_mask = G == 4 ? 0x03030303u : 0x0303u;
+        if ((codes & solid_mask) == 0) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) *reinterpret_cast<W*>(B16 + (int64_t)i * p.ps + cell0) = out[i];
+        } else {  // solid cells are never written
+#pragma unroll
+            for (int kk = 0; kk < G; ++kk) {
+                if ((codes >> (8 * kk)) & CODE_TYPE) continue;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    uint32_t word;
+                    if constexpr (G == 4) word = kk < 2 ? out[i].x : out[i].y;
+                    else word = out[i];
+                    B16[(int64_t)i * p.ps + cell0 + kk] = (uint16_t)(word >> (16 * (kk & 1)));
+                }
+            }
+        }
+    }
+}
+
+static bool tma_geometry(const LatticeParams& p, int G, TmaGeom& g) {
+    if (p.nx % 16 != 0) return false;
+    const int tile = tma_tile_cells(G);
+    int TX = 0;
+    for (int c : {512, 256, 128, 64, 32, 16})
+        if (c <= tile && p.nx % c == 0) {
+            TX = c;
+            break;
+        }
+    if (TX == 0) return false;
+    g.TX = TX;
+    g.R = tile / TX;
+    g.xchunks = p.nx / TX;
+    g.nrows = p.ny * p.nz;
+    g.ntiles = (int64_t)g.xchunks * ((g.nrows + g.R - 1) / g.R);
+    g.rb = (TX + 2 * TMA_HALO) * 2;
+    g.row_bytes = 19 * g.rb + TX;
+    g.stage_bytes = g.R * g.row_bytes;
+    return TMA_STAGES * g.stage_bytes <= tma_max_smem(G);
+}
+
+template <class S, bool FORCE, int G>
+static cudaError_t launch_tma16(const void* A, void* B, const uint8_t* code, const LatticeParams& p, const TmaGeom& g,
+                                cudaStream_t st) {
+    const size_t smem = (size_t)TMA_STAGES * g.stage_bytes;
+    auto kern = step_kernel_tma16<S, FORCE, G>;
+    // launch shape per (device, shared-memory size), computed once
+    struct Shape {
+        int dev;
+        size_t smem;
+        int sms, per_sm;
+    };
+    static thread_local Shape cache[8];
+    static thread_local int ncache = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int sms = 0, per_sm = 0;
+    for (int c = 0; c < ncache; ++c)
+        if (cache[c].dev == dev && cache[c].smem == smem) {
+            sms = cache[c].sms;
+            per_sm = cache[c].per_sm;
+        }
+    if (per_sm == 0) {
+        // The attribute is the kernel's maximum for every later launch, so it is
+        // set to the largest ring any tile geometry needs (TX = 16, R = 32),
+        // never lowered to the current one.
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tma_max_smem(G))) != cudaSuccess)
+            return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TMA_THREADS, smem)) != cudaSuccess)
+            return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        cache[ncache % 8] = Shape{dev, smem, sms, per_sm};
+        ++ncache;
+    }
+    int64_t grid = (int64_t)sms * per_sm;
+    if (grid > g.ntiles) grid = g.ntiles;
+    kern<<<(unsigned)grid, TMA_THREADS, smem, st>>>((const S*)A, (S*)B, code, p, g);
+    return cudaGetLastError();
+}
+
+template <class S, int G>
+static cudaError_t step_tma16_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p, int block,
+                                cudaStream_t st) {
+    TmaGeom g;
+    if (!tma_geometry(p, G, g) || p.err == nullptr) return step_rows_t<S, 0>(A, B, code, p, block, st);
+    const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
+    return force ? launch_tma16<S, true, G>(A, B, code, p, g, st) : launch_tma16<S, false, G>(A, B, code, p, g, st);
+}
+
+template <class S, int HINT>
+static cudaError_t step_rows_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p, int block,
                                cudaStream_t st) {
     int bx = block > 0 ? (block / 32) * 32 : 256;
     if (bx < 32) bx = 32;
@@ -450,6 +806,12 @@ static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* co
                     return variant == 8 ? step_quads16_t<S, 0>(A, B, code, p, block, st)
                                         : step_quads16_t<S, 1>(A, B, code, p, block, st);
             }
+            return step_rows_t<S, 0>(A, B, code, p, block, st);
+        case 10:
+        case 11:
+            if constexpr (sizeof(S) == 2)
+                return variant == 10 ? step_tma16_t<S, 4>(A, B, code, p, block, st)
+                                     : step_tma16_t<S, 2>(A, B, code, p, block, st);
             return step_rows_t<S, 0>(A, B, code, p, block, st);
         case 0:
             // measured defaults on GB300 (256^3): FP32 one cell per thread in

@@ -68,7 +68,7 @@ TINY = [
     (66, 5, 4, 0.7, 20, ("random", 22), (0.02, 0.0, 0.0), (0, 0, 0)),
 ]
 
-KERNELS = [1, 4, 6]
+KERNELS = [1, 4, 6, 10]
 
 
 def _flags(spec, nx, ny, nz):
@@ -91,12 +91,12 @@ def test_tiny_grids(case, storage, kernel, perm):
     check_pair(ora, gpu, storage, perm, flags)
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11])
 @pytest.mark.parametrize("storage", STORAGES)
 def test_every_variant(storage, kernel, perm):
     """Every step-kernel variant (cache policies, one or two cells per
     thread) on a grid with walls, lid and force, odd and even row lengths."""
-    for nx, ny, nz in ((34, 7, 6), (35, 6, 5), (136, 5, 4)):
+    for nx, ny, nz in ((34, 7, 6), (35, 6, 5), (136, 5, 4), (48, 5, 4)):
         flags = W.random_flags(nx, ny, nz, seed=nx, p_wall=0.15, p_lid=0.1)
         rho0, u0 = W.random_fields(nx, ny, nz, seed=7, du=0.05, drho=0.02)
         ora, gpu = run_pair(nx, ny, nz, 0.7, 12, storage, flags, (0.04, 0.01, -0.02), (1e-4, 0, 0),
@@ -229,4 +229,20 @@ def test_autotune_keeps_state(storage, perm, tmp_path, monkeypatch):
     assert again.autotune(reps=3) == (v, b, ms)  # from the cache
     ora.step(30)
     gpu.step(30)
+    check_pair(ora, gpu, storage, perm, flags)
+
+
+@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+@pytest.mark.parametrize("dims", [(32, 6, 5), (48, 5, 3), (64, 3, 4), (96, 5, 3), (512, 3, 2), (256, 4, 3)],
+                         ids=lambda d: "x".join(map(str, d)))
+@pytest.mark.parametrize("kernel", [10, 11])
+def test_tma_pipeline_variant(dims, storage, kernel, perm):
+    """Variant 10 (bulk copies into a shared-memory ring): tile widths 16..512
+    cells, partial last tiles, walls, lid and force, several steps."""
+    nx, ny, nz = dims
+    flags = W.random_flags(nx, ny, nz, seed=nx + ny, p_wall=0.1, p_lid=0.05)
+    rho0, u0 = W.random_fields(nx, ny, nz, seed=3, du=0.05, drho=0.02)
+    ora, gpu = run_pair(nx, ny, nz, 0.7, 9, storage, flags, (0.04, 0.0, 0.01), (1e-4, 0, -5e-5),
+                        rho0, u0, kernel=kernel)
+    gpu.sync()  # raises on a device-side wait timeout
     check_pair(ora, gpu, storage, perm, flags)
