@@ -62,6 +62,11 @@ def parse_args(argv=None):
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the library default variant instead of the autotuner's choice")
+    ap.add_argument("--workload", choices=["tgv", "serve"], default="tgv",
+                    help="tgv: the 256^3 Taylor-Green line (default); serve: a full serving run")
+    ap.add_argument("--serve-requests", type=int, default=80,
+                    help="requests in the serving section of the default line (0 = skip)")
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="HBM budget of the batch pool")
     return ap.parse_args(argv)
 
 
@@ -341,6 +346,44 @@ def run_ours(args, dist: Dist):
     return line
 
 
+# ---------------------------------------------------------------- serving
+def run_serving(n_requests, rate_multipliers=(2.0,), budget_gb=64.0, seed=16781, calib=16,
+                device=None):
+    """Continuous-batching serving of a seeded Poisson stream of cavity /
+    channel requests (sizes log-uniform 16^3..192^3, aspect <= 4, tau in
+    [0.52, 1], steps in [200, 5000], FP32 / shifted-FP16 50/50), against the
+    same stream served one plain FP32 lattice at a time.  Arrival rates are
+    set as multiples of the measured sequential FP32 capacity."""
+    import torch
+
+    from paper_2409_16781_gb300 import workloads as W
+    from paper_2409_16781_gb300.serve import BatchBackend, SequentialBackend, serve
+
+    torch.cuda.synchronize()
+    # sequential FP32 capacity: service time of the first `calib` requests
+    # presented at once (arrivals zeroed)
+    base = W.request_stream(n=n_requests, rate_hz=1.0, seed=seed)
+    cal = [W.Request(**{**r.__dict__, "arrival_s": 0.0}) for r in base[:calib]]
+    st = serve(cal, SequentialBackend("f32", device=device))
+    capacity = len(cal) / max(st.makespan, 1e-9)      # requests per second
+    out = {"requests": n_requests, "capacity_req_per_s": round(capacity, 3),
+           "hbm_budget_gb": budget_gb, "storage_mix": "f32/f16s 50/50 (batched); f32 (sequential)",
+           "policy": "batched: shortest remaining work first, 4M-cell occupancy target, 8 ms chunks, "
+                     "3 queued; sequential: FIFO, one lattice at a time, one launch per step",
+           "runs": []}
+    for mult in rate_multipliers:
+        reqs = W.request_stream(n=n_requests, rate_hz=mult * capacity, seed=seed)
+        be = BatchBackend(int(budget_gb * (1 << 30)), max_slots=1024, device=device)
+        sb = serve(reqs, be, policy="srpt", target_cells=4_000_000)
+        be.close()
+        torch.cuda.synchronize()
+        ss = serve(reqs, SequentialBackend("f32", device=device))
+        torch.cuda.synchronize()
+        out["runs"].append({"rate_multiplier": mult, "rate_hz": round(mult * capacity, 3),
+                            "batched": sb.summary(), "sequential_fp32": ss.summary()})
+    return out
+
+
 # ---------------------------------------------------------------- oracle
 def oracle_slab_run(n, planes, steps):
     """Run the FP64 oracle for `steps` steps on an n x n x planes slab of the
@@ -421,7 +464,15 @@ def main(argv=None):
         return 0
     dist = Dist()
     try:
+        if args.workload == "serve":
+            if dist.rank == 0:
+                print(json.dumps(serve_line(args)), flush=True)
+            return 0
         line = run_ours(args, dist)
+        if dist.rank == 0 and dist.world == 1 and args.serve_requests > 0:
+            line["serving"] = run_serving(args.serve_requests, (2.0,), args.serve_budget_gb)
+        elif dist.rank == 0:
+            line["serving"] = None
         if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.n)
         elif dist.rank == 0:
@@ -431,6 +482,21 @@ def main(argv=None):
     finally:
         dist.close()
     return 0
+
+
+def serve_line(args):
+    """A full serving run: the request stream at 0.5x and 2x the sequential
+    FP32 capacity; value = batched aggregate MLUPS at 2x."""
+    n = args.serve_requests if args.serve_requests > 0 else 2000
+    sv = run_serving(n, (0.5, 2.0), args.serve_budget_gb)
+    hi = sv["runs"][-1]
+    return {"metric": METRIC, "value": hi["batched"]["mlups"], "unit": "MLUPS", "n_gpus": 1,
+            "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f16", "data": "synthetic",
+            "config": {"workload": f"serving: {n} seeded Poisson cavity/channel requests, 16^3-192^3, "
+                                   f"tau U[0.52,1], steps U[200,5000]",
+                       "parallelism": "single"},
+            "serving": sv}
 
 
 def _single():

@@ -194,6 +194,85 @@ int lb_totals_static(const void *populations, int64_t plane_stride, const uint8_
                      int nx, int ny, int nz, int storage, const double *force,
                      const double *u_lid, void *stream, double *out);
 
+/* ---------------------------------------------------------------------
+ * Batches: many independent lattices advanced by shared launches (no
+ * counterpart in the paper, which runs one lattice; this is the serving
+ * form of the same update).  A batch owns one device pool; each admitted
+ * lattice ("slot") keeps its populations resident there with its own
+ * size, tau, storage, force, lid and step budget.  lb_batch_step(b, n)
+ * advances every slot that still has steps left by up to n steps: per step,
+ * one persistent kernel per storage type over all such slots (one thread
+ * per cell, the same pull-collide update as lb_step), then a one-block
+ * kernel that swaps each slot's A/B arrays and counts its steps down.
+ * Groups of 8 steps are replayed from a captured CUDA graph; membership
+ * lives in device memory, so the graph stays valid as slots come and go.
+ * ------------------------------------------------------------------- */
+typedef struct lb_batch lb_batch; /* opaque */
+
+/* Pool bytes one slot of this size and storage takes (0 on bad sizes). */
+size_t lb_batch_slot_bytes(int nx, int ny, int nz, int storage);
+/* Device bytes of a batch's fixed area (slot table, work lists, reduction
+ * scratch, 16 MiB host-transfer staging) for max_slots slots. */
+size_t lb_batch_fixed_bytes(int max_slots);
+
+/* Create a batch with a pool of capacity_bytes (the HBM budget for slots)
+ * and up to max_slots (1..65536) slots; the library allocates fixed area +
+ * pool with cudaMalloc.  stream: cudaStream_t to issue work on; NULL makes
+ * the batch create and own a non-blocking stream (CUDA graphs cannot be
+ * captured on the legacy default stream). */
+int lb_batch_create(lb_batch **out, size_t capacity_bytes, int max_slots, void *stream);
+/* As lb_batch_create, with all device memory from the caller's buffer
+ * (256-byte aligned; the pool is what remains after the fixed area). */
+int lb_batch_create_in(lb_batch **out, void *device_buffer, size_t bytes, int max_slots, void *stream);
+
+/* Admit a lattice: arguments as lb_create (opt: storage and force), plus
+ * the number of steps it is to take.  Starts at rest (f = w).  Returns the
+ * slot id in *slot.  LB_ENOMEM: it does not fit the pool's free space;
+ * LB_EBUSY: all slots in use; LB_EINVAL: bad arguments.  Synchronises. */
+int lb_batch_add(lb_batch *b, int nx, int ny, int nz, double tau, const double *u_lid,
+                 const uint8_t *flags, const lb_options *opt, int64_t steps, int *slot);
+/* Set a slot's remaining step count. */
+int lb_batch_set_steps(lb_batch *b, int slot, int64_t steps);
+/* Set the step counters of n slots at once (one upload, ordered after the
+ * work already queued): used by schedulers that grant step quotas per
+ * chunk.  A slot whose counter is 0 is skipped by lb_batch_step.  A slot
+ * reported finished by lb_batch_poll may be read back (lb_batch_fetch) or
+ * removed only if the caller grants it no further steps. */
+int lb_batch_set_steps_many(lb_batch *b, int n, const int *slots, const int64_t *steps);
+/* As lb_init_fields, for one slot. */
+int lb_batch_init_fields(lb_batch *b, int slot, const double *rho, const double *u);
+/* Advance every slot with steps left by up to n steps (asynchronous). */
+int lb_batch_step(lb_batch *b, int n);
+/* Slots that have taken all their steps and are still admitted: up to max
+ * ids into done_slots, their total count in *ndone.  Synchronises. */
+int lb_batch_poll(lb_batch *b, int *done_slots, int max, int *ndone);
+/* Remaining and taken steps, dims[3], storage of a slot (outputs may be NULL). */
+int lb_batch_query(lb_batch *b, int slot, int64_t *remaining, int64_t *done, int *dims, int *storage);
+/* As lb_moments / lb_totals / lb_get_populations, for one slot. */
+int lb_batch_moments(lb_batch *b, int slot, double *rho, double *u);
+int lb_batch_totals(lb_batch *b, int slot, double *mass, double *mom);
+int lb_batch_get_populations(lb_batch *b, int slot, double *f);
+/* Asynchronous read-back of a finished slot (no steps left): rho (N) and u
+ * (3N SoA) into caller host buffers, which must stay valid until
+ * lb_batch_fetch_done reports 1 (pinned buffers make the copy truly
+ * asynchronous).  Runs on the batch's io stream while queued steps go on;
+ * the slot's spare population array is the device-side scratch.
+ * LB_EBUSY if the slot still has steps. */
+int lb_batch_fetch(lb_batch *b, int slot, double *rho, double *u);
+/* 1 when the slot's fetch has completed, 0 while pending, <0 on error. */
+int lb_batch_fetch_done(lb_batch *b, int slot);
+/* Retire a slot and return its memory to the pool (waits for its fetch;
+ * drains queued work only if the slot still had steps). */
+int lb_batch_remove(lb_batch *b, int slot);
+/* Free pool bytes and free slots (either may be NULL). */
+int lb_batch_free_bytes(lb_batch *b, size_t *free_bytes, int *free_slots);
+/* Wait for the batch's stream. */
+int lb_batch_sync(lb_batch *b);
+/* Release the batch (and its memory if the library allocated it). */
+int lb_batch_destroy(lb_batch *b);
+/* Description of the last batch failure on the calling thread. */
+const char *lb_batch_last_error(void);
+
 /* Wait for all work issued on the lattice's stream.  Returns LB_ETIMEOUT
  * (and clears the condition) if a kernel's bounded wait on an asynchronous
  * copy gave up since the last check. */

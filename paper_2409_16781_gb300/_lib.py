@@ -61,6 +61,27 @@ SIGNATURES = {
     "lb_set_kernel": (_I, [_P, _I, _I]),
     "lb_autotune": (_I, [_P, _I, _P, _P, _P]),
     "lb_totals_static": (_I, [_P, _I64, _P, _I, _I, _I, _I, _P, _P, _P, _P]),
+    "lb_batch_slot_bytes": (_S, [_I, _I, _I, _I]),
+    "lb_batch_fixed_bytes": (_S, [_I]),
+    "lb_batch_create": (_I, [_P, _S, _I, _P]),
+    "lb_batch_create_in": (_I, [_P, _P, _S, _I, _P]),
+    "lb_batch_add": (_I, [_P, _I, _I, _I, _D, _P, _P, _P, _I64, _P]),
+    "lb_batch_set_steps": (_I, [_P, _I, _I64]),
+    "lb_batch_set_steps_many": (_I, [_P, _I, _P, _P]),
+    "lb_batch_init_fields": (_I, [_P, _I, _P, _P]),
+    "lb_batch_step": (_I, [_P, _I]),
+    "lb_batch_poll": (_I, [_P, _P, _I, _P]),
+    "lb_batch_query": (_I, [_P, _I, _P, _P, _P, _P]),
+    "lb_batch_moments": (_I, [_P, _I, _P, _P]),
+    "lb_batch_totals": (_I, [_P, _I, _P, _P]),
+    "lb_batch_get_populations": (_I, [_P, _I, _P]),
+    "lb_batch_fetch": (_I, [_P, _I, _P, _P]),
+    "lb_batch_fetch_done": (_I, [_P, _I]),
+    "lb_batch_remove": (_I, [_P, _I]),
+    "lb_batch_free_bytes": (_I, [_P, _P, _P]),
+    "lb_batch_sync": (_I, [_P]),
+    "lb_batch_destroy": (_I, [_P]),
+    "lb_batch_last_error": (ctypes.c_char_p, []),
     "lb_sync": (_I, [_P]),
     "lb_query": (_I, [_P, _P, _P, _P]),
     "lb_destroy": (_I, [_P]),

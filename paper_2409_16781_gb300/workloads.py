@@ -197,9 +197,15 @@ class Request:
         return self.nx * self.ny * self.nz
 
     def flags(self) -> np.ndarray:
-        if self.kind == "cavity":
-            return cavity_flags(self.nx, self.ny, self.nz)
-        return channel_flags(self.nx, self.ny, self.nz, walls=("y", "z"))
+        """The request's geometry (built once, then kept with the request)."""
+        f = self.extra.get("flags")
+        if f is None:
+            if self.kind == "cavity":
+                f = cavity_flags(self.nx, self.ny, self.nz)
+            else:
+                f = channel_flags(self.nx, self.ny, self.nz, walls=("y", "z"))
+            self.extra["flags"] = f
+        return f
 
 
 def request_stream(n: int = 2000, rate_hz: float = 10.0, seed: int = 16781,

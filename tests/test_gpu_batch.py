@@ -1,0 +1,190 @@
+"""Batches of lattices (lb_batch_*): every lattice gives the same result alone
+and in the mix, per-slot step budgets, the captured-graph path, HBM-budget
+admission, and the serving loop end to end.
+
+Tolerances as in the parity tests: f64 populations 1e-12 relative; the
+others compare velocity fields, max |du| / max |u| <= 1e-5 (f32), 2e-3
+(f16s), 3e-2 (bf16s).  A lattice alone runs through lb_step (one thread per
+cell, variant 1); in the batch it runs the batched kernel with other
+lattices of other sizes and storage types.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from parity import fluid_mask, lib_to_oracle_perm, pop_rel_err, to_lib_order, vel_err
+from paper_2409_16781_gb300 import Lattice, LbError
+from paper_2409_16781_gb300 import _lib as L
+from paper_2409_16781_gb300 import workloads as W
+from paper_2409_16781_gb300.batch import Batch, slot_bytes
+from paper_2409_16781_gb300.serve import BatchBackend, SequentialBackend, serve
+
+pytestmark = pytest.mark.gpu
+
+VEL_TOL = {"f32": 1e-5, "f16s": 2e-3, "bf16s": 3e-2}
+# relative mass agreement: the storage rounding of each deviation bounds how
+# closely two kernels' conserved sums agree (16-bit: about one ulp per cell)
+MASS_TOL = {"f64": 1e-12, "f32": 1e-8, "f16s": 1e-5, "bf16s": 1e-4}
+
+MIX = [
+    # nx, ny, nz, tau, storage, kind, steps
+    (17, 12, 9, 0.7, "f32", "cavity", 40),
+    (32, 20, 16, 0.56, "f16s", "channel", 33),
+    (9, 7, 13, 0.9, "f64", "cavity", 25),
+    (40, 10, 12, 0.6, "bf16s", "channel", 30),
+    (24, 24, 24, 0.52, "f32", "channel", 57),
+    (5, 31, 6, 0.8, "f16s", "cavity", 11),
+    (64, 3, 2, 0.65, "f32", "random", 21),
+]
+
+
+def _geom(nx, ny, nz, kind):
+    if kind == "cavity":
+        return W.cavity_flags(nx, ny, nz), (0.06, 0.0, 0.0), (0.0, 0.0, 0.0)
+    if kind == "channel":
+        return W.channel_flags(nx, ny, nz, walls=("y", "z")), (0.0, 0.0, 0.0), (2e-5, 0.0, 0.0)
+    return W.random_flags(nx, ny, nz, seed=nx, p_wall=0.1, p_lid=0.05), (0.03, 0.01, 0.0), (1e-5, 0, 1e-5)
+
+
+def _compare(f_batch, f_alone, u_batch, u_alone, storage, flags, shape):
+    mask = fluid_mask(flags, shape)
+    if storage == "f64":
+        assert pop_rel_err(f_batch, f_alone, mask) <= 1e-12
+    else:
+        assert vel_err(u_batch, u_alone, mask) <= VEL_TOL[storage]
+
+
+def test_same_alone_and_in_the_mix():
+    b = Batch(capacity_bytes=64 << 20, max_slots=16)
+    slots = []
+    for nx, ny, nz, tau, storage, kind, steps in MIX:
+        flags, ulid, g = _geom(nx, ny, nz, kind)
+        s = b.add(nx, ny, nz, tau, steps, u_lid=ulid, flags=flags, storage=storage, force=g)
+        slots.append(s)
+    b.step(60)          # more than any budget: each slot stops at its own count
+    done = set(b.poll())
+    assert done == set(slots)
+    bitwise = 0
+    for s, (nx, ny, nz, tau, storage, kind, steps) in zip(slots, MIX):
+        q = b.query(s)
+        assert q["done"] == steps and q["remaining"] == 0
+        flags, ulid, g = _geom(nx, ny, nz, kind)
+        alone = Lattice(nx, ny, nz, tau, u_lid=ulid, flags=flags, storage=storage, force=g, kernel=1)
+        alone.step(steps)
+        fb, fa = b.populations(s), alone.populations()
+        _, ub = b.moments(s)
+        _, ua = alone.moments()
+        _compare(fb, fa, ub, ua, storage, flags, alone.shape)
+        mask = fluid_mask(flags, alone.shape)
+        bitwise += int(np.array_equal(fb[:, mask], fa[:, mask]))
+        mb, _ = b.totals(s)
+        ma, _ = alone.totals()
+        assert abs(mb - ma) <= MASS_TOL[storage] * ma
+        alone.close()
+    print(f"bitwise-identical slots: {bitwise}/{len(MIX)}")
+    b.close()
+
+
+def test_batch_matches_oracle_f64():
+    perm = lib_to_oracle_perm()
+    b = Batch(capacity_bytes=16 << 20, max_slots=4)
+    cases = [(11, 9, 7, 0.65, "cavity", 30), (16, 6, 10, 0.8, "random", 19)]
+    slots = []
+    for nx, ny, nz, tau, kind, steps in cases:
+        flags, ulid, g = _geom(nx, ny, nz, kind)
+        slots.append(b.add(nx, ny, nz, tau, steps, u_lid=ulid, flags=flags, storage="f64", force=g))
+    b.step(31)
+    for s, (nx, ny, nz, tau, kind, steps) in zip(slots, cases):
+        flags, ulid, g = _geom(nx, ny, nz, kind)
+        ora = O.Lattice(nx, ny, nz, tau, u_lid=ulid, flags=flags, force=g)
+        ora.step(steps)
+        err = pop_rel_err(b.populations(s), to_lib_order(ora.A, perm), fluid_mask(flags, (nz, ny, nx)))
+        assert err <= 1e-12
+    b.close()
+
+
+def test_graph_path_and_init_fields():
+    """Step counts above the graph size (8) replay captured graphs; the
+    result equals the single-lattice run."""
+    nx, ny, nz = 20, 14, 12
+    rho0, u0 = W.random_fields(nx, ny, nz, seed=4, du=0.04, drho=0.01)
+    b = Batch(capacity_bytes=16 << 20, max_slots=4)
+    s = b.add(nx, ny, nz, 0.6, 1000, storage="f32")
+    b.init_fields(s, rho0, u0)
+    b.step(8 * 5 + 3)
+    assert b.query(s)["done"] == 43
+    alone = Lattice(nx, ny, nz, 0.6, storage="f32", kernel=1)
+    alone.init_fields(rho0, u0)
+    alone.step(43)
+    _, ub = b.moments(s)
+    _, ua = alone.moments()
+    assert vel_err(ub, ua, np.ones((nz, ny, nx), bool)) <= 1e-5
+    b.close()
+
+
+def test_admission_limits():
+    nbytes = slot_bytes(16, 16, 16, "f32")
+    small_bytes = slot_bytes(4, 4, 4, "f32")
+    assert small_bytes < nbytes
+    b = Batch(capacity_bytes=2 * nbytes + small_bytes, max_slots=3)
+    s0 = b.add(16, 16, 16, 0.7, 10)
+    s1 = b.add(16, 16, 16, 0.7, 10)
+    with pytest.raises(LbError) as e:
+        b.add(16, 16, 16, 0.7, 10)
+    assert e.value.status == L.LB_ENOMEM
+    assert b.try_add(16, 16, 16, 0.7, 10) is None
+    small = b.add(4, 4, 4, 0.7, 10)          # still fits
+    with pytest.raises(LbError) as e:
+        b.add(2, 2, 2, 0.7, 10)
+    assert e.value.status == L.LB_EBUSY       # 3 slots in use
+    b.remove(s0)
+    s2 = b.add(16, 16, 16, 0.7, 10)           # memory and slot came back
+    assert s2 == s0
+    b.step(10)
+    assert set(b.poll()) == {s1, s2, small}
+    for s in (s1, s2, small):
+        b.remove(s)
+    free_bytes, free_slots = b.free()
+    assert free_slots == 3 and free_bytes == 2 * nbytes + small_bytes  # fully coalesced
+    b.close()
+
+
+@pytest.mark.parametrize("policy", ["fifo", "srpt"])
+def test_serve_end_to_end_same_as_sequential(policy):
+    """A small request stream through the batched server and through the
+    one-at-a-time baseline (same storage per request) gives the same
+    velocity fields (checksums), and every request completes."""
+    reqs = W.request_stream(n=10, rate_hz=200.0, seed=5, min_cells=6 ** 3, max_cells=20 ** 3,
+                            steps_range=(20, 120))
+    be = BatchBackend(capacity_bytes=128 << 20, max_slots=8, keep_fields=True)
+    st = serve(reqs, be, chunk_ms=2.0, policy=policy, target_cells=5000)
+    be.close()
+    assert len(st.results) == len(reqs) and not st.rejected
+    got = {r.rid: r.checksum for r in st.results}
+    for req in reqs:
+        seq = SequentialBackend(storage=req.storage, keep_fields=True)
+        st1 = serve([req], seq)
+        ref = st1.results[0].checksum
+        tol = 1e-5 if req.storage == "f32" else 2e-3
+        assert abs(got[req.rid] - ref) <= tol * max(ref, 1e-12) + 1e-12
+    s = st.summary()
+    assert s["requests"] == len(reqs) and s["p99_s"] >= s["p50_s"]
+
+
+def test_step_quotas():
+    """lb_batch_set_steps_many grants per-slot quotas: a slot with quota 0 is
+    not stepped; quotas are consumed by the steps that follow."""
+    b = Batch(capacity_bytes=16 << 20, max_slots=4)
+    s0 = b.add(12, 10, 8, 0.7, 0, flags=W.cavity_flags(12, 10, 8), u_lid=(0.05, 0, 0))
+    s1 = b.add(12, 10, 8, 0.7, 0, flags=W.cavity_flags(12, 10, 8), u_lid=(0.05, 0, 0))
+    b.set_steps_many([s0, s1], [7, 0])
+    b.step(10)
+    b.set_steps_many([s1], [3])
+    b.step(10)
+    assert b.query(s0)["done"] == 7 and b.query(s1)["done"] == 3
+    a7 = Lattice(12, 10, 8, 0.7, flags=W.cavity_flags(12, 10, 8), u_lid=(0.05, 0, 0), kernel=1)
+    a7.step(7)
+    _, u0 = b.moments(s0)
+    _, ua = a7.moments()
+    assert vel_err(u0, ua, W.cavity_flags(12, 10, 8) == 0) <= 1e-5
+    b.close()
