@@ -71,9 +71,7 @@ __device__ __forceinline__ void update_cell(const SlotDev& sd, int parity, int c
     S* B = static_cast<S*>(sd.pop[parity ^ 1]);
     M d[Q];
     pull_cell<S>(A, sd.code, sd.p, x, y, z, cell, cc, d);
-    M drho, rho, ux, uy, uz;
-    macro_dev<M>(d, sd.p, drho, rho, ux, uy, uz);
-    collide_dev<M, FORCE>(d, sd.p, drho, rho, ux, uy, uz);
+    relax_dev<M, FORCE>(d, sd.p);
 #pragma unroll
     for (int i = 0; i < Q; ++i) B[(int64_t)i * sd.p.ps + cell] = Storage<S>::store(d[i]);
 }

@@ -120,10 +120,12 @@ __device__ __forceinline__ void moment_sums(const M (&d)[Q], M& drho, M& jx, M& 
     drho = s;
 }
 
-// 1/rho: IEEE division in FP64; in FP32 the approximate reciprocal (about
-// 2 ulp) -- far below the FP32 tolerance and several instructions shorter.
+// 1/rho, correctly rounded.  An approximate reciprocal is not good enough:
+// its error has a sign bias, so the equilibrium momentum rho u falls short
+// of j by a fixed fraction every step and the collision drains momentum
+// (an artificial dissipation that builds up over thousands of steps).
 __device__ __forceinline__ double recip(double r) { return 1.0 / r; }
-__device__ __forceinline__ float recip(float r) { return __fdividef(1.0f, r); }
+__device__ __forceinline__ float recip(float r) { return __frcp_rn(r); }
 
 // Density and half-force-shifted velocity u = j/rho + g/2 from deviations.
 template <class M>
@@ -138,17 +140,43 @@ __device__ __forceinline__ void macro_dev(const M (&d)[Q], const LatticeParams& 
     uz = jz * inv + M(0.5) * (M)p.g[2];
 }
 
-// BGK relaxation towards f^eq (Eq. 2-3) plus the Guo source term, in place:
+// BGK relaxation towards f^eq (Eq. 2-3) plus the Guo source term (the S_i
+// of Eq. 1), in place, computing the moments itself:
 //   d_i <- (1 - omega) d_i + omega deq_i + S_i,
 //   deq_i = f^eq_i - w_i = w_i (drho + rho (3 cu + 4.5 cu^2 - 1.5 uu)),
-//   S_i   = (1 - omega/2) w_i [3(c_i - u) + 9 (c_i.u) c_i] . (rho g).
-// For an opposite pair (i, i') c_i' = -c_i, so both terms split into a part
-// even in c (shared) and a part odd in c (sign-flipped):
-//   even: w (drho + rho (4.5 cu^2 - 1.5 uu)),  (1-omega/2) w (9 cu cF - 3 uF)
-//   odd : 3 w rho cu,                          (1-omega/2) 3 w cF.
+//   S_i   = (1 - omega/2) w_i [3(c_i - u) + 9 (c_i.u) c_i] . F,  F = rho g,
+//   u = j / rho + g / 2.
+// It works on opposite pairs (i, i'), c_i' = -c_i: the pair sum relaxes with
+// the part of deq + S even in c, the pair difference with the odd part.  In
+// exact arithmetic this collision conserves mass and moves the momentum
+// from j to j + F; in finite precision the rounded weights (1/18, 1/36 are
+// not representable) would bias both by a fixed fraction every step.  So the
+// three axis pairs take the difference that makes the momentum exactly
+// j + F, and the rest population the value that keeps the mass: the same
+// collision, with the conservation laws holding to rounding.
 template <class M, bool FORCE>
-__device__ __forceinline__ void collide_dev(M (&d)[Q], const LatticeParams& p, M drho, M rho, M ux,
-                                            M uy, M uz) {
+__device__ __forceinline__ void relax_dev(M (&d)[Q], const LatticeParams& p) {
+    // pre-collision pair sums / differences and moments
+    M ps[9], pd[9];
+    M drho = d[0], jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const int i = 2 * k + 1;
+        ps[k] = d[i] + d[i + 1];
+        pd[k] = d[i] - d[i + 1];
+        drho += ps[k];
+        if (D3Q19::cx(i) == 1) jx += pd[k];
+        if (D3Q19::cx(i) == -1) jx -= pd[k];
+        if (D3Q19::cy(i) == 1) jy += pd[k];
+        if (D3Q19::cy(i) == -1) jy -= pd[k];
+        if (D3Q19::cz(i) == 1) jz += pd[k];
+        if (D3Q19::cz(i) == -1) jz -= pd[k];
+    }
+    const M rho = M(1) + drho;
+    const M inv = recip(rho);
+    const M ux = jx * inv + M(0.5) * (M)p.g[0];
+    const M uy = jy * inv + M(0.5) * (M)p.g[1];
+    const M uz = jz * inv + M(0.5) * (M)p.g[2];
     const M om = (M)p.omega;
     const M omc = M(1) - om;
     const M uu15 = M(1.5) * (ux * ux + uy * uy + uz * uz);
@@ -160,32 +188,31 @@ __device__ __forceinline__ void collide_dev(M (&d)[Q], const LatticeParams& p, M
         uF = ux * Fx + uy * Fy + uz * Fz;
         pref = M(1) - M(0.5) * om;
     }
-    // per weight class W: even = aW cu^2 + bW (+ force), odd = cW cu (+ force)
-    //   aW = 4.5 omega W rho, bW = omega W (drho - 1.5 rho uu), cW = 3 omega W rho
+    // Half the post-collision pair sums (hs) and differences (hd):
+    //   hs = (1 - omega)/2 (d_i + d_i') + even,   hd = (1 - omega)/2 (d_i - d_i') + odd,
+    //   d_i = hs + hd,  d_i' = hs - hd,  per weight class W:
+    //   even = omega W (rho (4.5 cu^2 - 1.5 uu) + drho) [+ pref W (9 cu cF - 3 uF)]
+    //   odd  = 3 omega W rho cu                         [+ 3 pref W cF]
     const M wa = (M)D3Q19::w(1), wb = (M)D3Q19::w(7);
+    const M omh = M(0.5) * omc;
     const M orho = om * rho;
     const M base = om * (drho - rho * uu15);
-    const M a1 = M(4.5) * wa * orho, b1 = wa * base, c1 = M(3) * wa * orho;
+    const M a1 = M(4.5) * wa * orho, b1 = wa * base;
     const M a2 = M(4.5) * wb * orho, b2 = wb * base, c2 = M(3) * wb * orho;
-    M fa1 = 0, fb1 = 0, fc1 = 0, fa2 = 0, fb2 = 0, fc2 = 0;
-    if (FORCE) {  // Guo: even (1-omega/2) W (9 cu cF - 3 uF), odd (1-omega/2) 3 W cF
+    M fa1 = 0, fb1 = 0, fa2 = 0, fb2 = 0, fc2 = 0;
+    if (FORCE) {
         fa1 = M(9) * pref * wa;
         fb1 = M(-3) * pref * wa * uF;
-        fc1 = M(3) * pref * wa;
         fa2 = M(9) * pref * wb;
         fb2 = M(-3) * pref * wb * uF;
         fc2 = M(3) * pref * wb;
     }
-    {
-        const M w0 = (M)D3Q19::w(0);
-        M e = w0 * base;
-        if (FORCE) e += pref * w0 * (M(-3) * uF);
-        d[0] = omc * d[0] + e;
-    }
+    M hs[9], hd[9];
+    M ox = 0, oy = 0, oz = 0;  // half the momentum carried by the 12 diagonal directions
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const int i = 2 * k + 1;
-        const bool axis = i <= 6;
+        const bool axis = k < 3;
         M cu = 0, cF = 0;
         if (D3Q19::cx(i) == 1) { cu += ux; cF += Fx; }
         if (D3Q19::cx(i) == -1) { cu -= ux; cF -= Fx; }
@@ -194,13 +221,32 @@ __device__ __forceinline__ void collide_dev(M (&d)[Q], const LatticeParams& p, M
         if (D3Q19::cz(i) == 1) { cu += uz; cF += Fz; }
         if (D3Q19::cz(i) == -1) { cu -= uz; cF -= Fz; }
         M even = (axis ? a1 : a2) * (cu * cu) + (axis ? b1 : b2);
-        M odd = (axis ? c1 : c2) * cu;
-        if (FORCE) {
-            even += (axis ? fa1 : fa2) * (cu * cF) + (axis ? fb1 : fb2);
-            odd += (axis ? fc1 : fc2) * cF;
+        if (FORCE) even += (axis ? fa1 : fa2) * (cu * cF) + (axis ? fb1 : fb2);
+        hs[k] = omh * ps[k] + even;
+        if (!axis) {
+            M odd = c2 * cu;
+            if (FORCE) odd += fc2 * cF;
+            hd[k] = omh * pd[k] + odd;
+            if (D3Q19::cx(i) == 1) ox += hd[k];
+            if (D3Q19::cx(i) == -1) ox -= hd[k];
+            if (D3Q19::cy(i) == 1) oy += hd[k];
+            if (D3Q19::cy(i) == -1) oy -= hd[k];
+            if (D3Q19::cz(i) == 1) oz += hd[k];
+            if (D3Q19::cz(i) == -1) oz -= hd[k];
         }
-        d[i] = omc * d[i] + (even + odd);
-        d[i + 1] = omc * d[i + 1] + (even - odd);
+    }
+    // axis pairs (1,2) x, (3,4) y, (5,6) z: post-collision momentum j + F
+    hd[0] = M(0.5) * (jx + Fx) - ox;
+    hd[1] = M(0.5) * (jy + Fy) - oy;
+    hd[2] = M(0.5) * (jz + Fz) - oz;
+    M msum = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) msum += hs[k];
+    d[0] = drho - M(2) * msum;  // mass unchanged by the collision
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        d[2 * k + 1] = hs[k] + hd[k];
+        d[2 * k + 2] = hs[k] - hd[k];
     }
 }
 

@@ -36,9 +36,7 @@ __global__ void __launch_bounds__(512) step_kernel_rows(const S* __restrict__ A,
     if (cc & CODE_TYPE) return;  // solid cells are never written
     M d[Q];
     pull_cell<S, HINT>(A, code, p, x, y, z, cell, cc, d);
-    M drho, rho, ux, uy, uz;
-    macro_dev<M>(d, p, drho, rho, ux, uy, uz);
-    collide_dev<M, FORCE>(d, p, drho, rho, ux, uy, uz);
+    relax_dev<M, FORCE>(d, p);
 #pragma unroll
     for (int i = 0; i < Q; ++i) st_pop<HINT>(B + (int64_t)i * p.ps + cell, Storage<S>::store(d[i]));
 }
@@ -128,14 +126,10 @@ __global__ void __launch_bounds__(256) step_kernel_pairs(const S* __restrict__ A
     if (c0 & CODE_NEAR_WALL) bounce_fix<S, HINT>(A, code, p, x0, y, z, cell0, d0);
     if (c1 & CODE_NEAR_WALL) bounce_fix<S, HINT>(A, code, p, x0 + 1, y, z, cell0 + 1, d1);
     {
-        M drho, rho, ux, uy, uz;
-        macro_dev<M>(d0, p, drho, rho, ux, uy, uz);
-        collide_dev<M, FORCE>(d0, p, drho, rho, ux, uy, uz);
+        relax_dev<M, FORCE>(d0, p);
     }
     {
-        M drho, rho, ux, uy, uz;
-        macro_dev<M>(d1, p, drho, rho, ux, uy, uz);
-        collide_dev<M, FORCE>(d1, p, drho, rho, ux, uy, uz);
+        relax_dev<M, FORCE>(d1, p);
     }
     const bool f0 = !(c0 & CODE_TYPE), f1 = !(c1 & CODE_TYPE);
     if (f0 && f1) {
@@ -246,9 +240,7 @@ __global__ void __launch_bounds__(256, 3) step_kernel_pairs16(const S* __restric
 #pragma unroll
         for (int i = 0; i < Q; ++i) d[i] = lo16<S>(v[i]);
         if (c0 & CODE_NEAR_WALL) bounce_fix<S, HINT>(A, code, p, x0, y, z, cell0, d);
-        float drho, rho, ux, uy, uz;
-        macro_dev<float>(d, p, drho, rho, ux, uy, uz);
-        collide_dev<float, FORCE>(d, p, drho, rho, ux, uy, uz);
+        relax_dev<float, FORCE>(d, p);
 #pragma unroll
         for (int i = 0; i < Q; ++i) out[i] = to16<S>(d[i]);
     }
@@ -257,9 +249,7 @@ __global__ void __launch_bounds__(256, 3) step_kernel_pairs16(const S* __restric
 #pragma unroll
         for (int i = 0; i < Q; ++i) d[i] = hi16<S>(v[i]);
         if (c1 & CODE_NEAR_WALL) bounce_fix<S, HINT>(A, code, p, x0 + 1, y, z, cell0 + 1, d);
-        float drho, rho, ux, uy, uz;
-        macro_dev<float>(d, p, drho, rho, ux, uy, uz);
-        collide_dev<float, FORCE>(d, p, drho, rho, ux, uy, uz);
+        relax_dev<float, FORCE>(d, p);
 #pragma unroll
         for (int i = 0; i < Q; ++i) out[i] |= to16<S>(d[i]) << 16;
     }
@@ -359,9 +349,7 @@ __global__ void __launch_bounds__(128, 4) step_kernel_quads16(const S* __restric
         for (int i = 0; i < Q; ++i) d[i] = get16<S>(v[i], k);
         const uint8_t ck = (uint8_t)(codes >> (8 * k));
         if (ck & CODE_NEAR_WALL) bounce_fix<S, HINT>(A, code, p, x0 + k, y, z, cell0 + k, d);
-        float drho, rho, ux, uy, uz;
-        macro_dev<float>(d, p, drho, rho, ux, uy, uz);
-        collide_dev<float, FORCE>(d, p, drho, rho, ux, uy, uz);
+        relax_dev<float, FORCE>(d, p);
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const uint32_t h = to16<S>(d[i]) << (16 * (k & 1));
@@ -654,9 +642,7 @@ __global__ void __launch_bounds__(TMA_THREADS, G == 4 ? 2 : 4) step_kernel_tma16
             }
             const uint8_t ck = (uint8_t)(codes >> (8 * kk));
             if (ck & CODE_NEAR_WALL) bounce_fix<S, 0>(A, code, p, xq + kk, y, z, cell0 + kk, d);
-            float drho, rho, ux, uy, uz;
-            macro_dev<float>(d, p, drho, rho, ux, uy, uz);
-            collide_dev<float, FORCE>(d, p, drho, rho, ux, uy, uz);
+            relax_dev<float, FORCE>(d, p);
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 const uint32_t h = to16<S>(d[i]) << (16 * (kk & 1));
