@@ -62,8 +62,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the library default variant instead of the autotuner's choice")
-    ap.add_argument("--workload", choices=["tgv", "serve"], default="tgv",
-                    help="tgv: the 256^3 Taylor-Green line (default); serve: a full serving run")
+    ap.add_argument("--workload", choices=["tgv", "serve", "porous", "precision"], default="tgv",
+                    help="tgv: the 256^3 Taylor-Green line (default); serve: a full serving run; "
+                         "porous: the 512^3 porous channel; precision: the 768^3 cavity precision study")
+    ap.add_argument("--taus", default="0.52,0.56,0.6", help="relaxation times of the precision study")
     ap.add_argument("--serve-requests", type=int, default=80,
                     help="requests in the serving section of the default line (0 = skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="HBM budget of the batch pool")
@@ -214,15 +216,16 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def ncu_traffic(profile_key: str):
+def ncu_traffic(profile_key: str, variant=None):
     """Per-launch DRAM bytes from a committed ncu summary, if it was taken
-    on the current kernel sources."""
+    on the current kernel sources and for the kernel variant being timed."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as fh:
             d = json.load(fh)
         rec = d.get(profile_key)
-        if rec and rec.get("source_hash") == kernel_source_hash():
+        if rec and rec.get("source_hash") == kernel_source_hash() and \
+                (variant is None or rec.get("variant") == variant):
             return rec.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
@@ -316,7 +319,7 @@ def run_ours(args, dist: Dist):
     achieved = bpu * N / (kernel_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-            "traffic": ncu_traffic(f"step_{args.storage}_tgv{n}"),
+            "traffic": ncu_traffic(f"step_{args.storage}_tgv{n}", tuned[0] if tuned else args.kernel),
             "algorithmic_bytes_per_launch": bpu * N, "kernel": "lb step kernel",
             "kernel_ms_mean": round(kernel_ms, 5), "kernel_ms_median": round(statistics.median(step_ms), 5)}
 
@@ -464,9 +467,10 @@ def main(argv=None):
         return 0
     dist = Dist()
     try:
-        if args.workload == "serve":
+        if args.workload in ("serve", "porous", "precision"):
+            fn = {"serve": serve_line, "porous": porous_line, "precision": precision_line}[args.workload]
             if dist.rank == 0:
-                print(json.dumps(serve_line(args)), flush=True)
+                print(json.dumps(fn(args)), flush=True)
             return 0
         line = run_ours(args, dist)
         if dist.rank == 0 and dist.world == 1 and args.serve_requests > 0:
@@ -482,6 +486,124 @@ def main(argv=None):
     finally:
         dist.close()
     return 0
+
+
+def porous_line(args):
+    """Porous channel 512^3, FP32, tau 0.8, g = 1e-6 x, walls on the y/z faces,
+    400 spheres (radius U[8,24], SplitMix64 seed 2409): MLUPS over all cells
+    and over fluid cells, CUDA events on the lattice's stream."""
+    import torch
+
+    from paper_2409_16781_gb300 import Lattice
+    from paper_2409_16781_gb300 import workloads as W
+    n = 512
+    flags = W.porous_flags(n, n, n, n_spheres=400, r_min=8, r_max=24, seed=2409)
+    fluid = int((flags == 0).sum())
+    stream = torch.cuda.current_stream()
+    lat = Lattice(n, n, n, 0.8, flags=flags, storage=args.storage, force=(1e-6, 0.0, 0.0), stream=stream)
+    tuned = lat.autotune(reps=10, cache=False)
+    for _ in range(args.warmup):
+        lat.step(1)
+    m0, _ = lat.totals()
+    K = args.steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    m1, p1 = lat.totals()
+    N = n ** 3
+    bpu = bytes_per_update(args.storage)
+    peak, kind = measured_peaks()
+    lat.close()
+    return {"metric": METRIC, "value": round(N * K / sec / 1e6, 1), "unit": "MLUPS", "n_gpus": 1, "steps": K,
+            "warmup": args.warmup, "ms_per_step": round(sec * 1e3 / K, 5), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": "porous channel 512^3, D3Q19 BGK, tau 0.8, g 1e-6 x, 400 spheres r U[8,24]",
+                       "solid_fraction": round(1 - fluid / N, 4),
+                       "kernel": {"variant": tuned[0], "block": tuned[1], "chosen_by": "lb_autotune"}},
+            "fluid_mlups": round(fluid * K / sec / 1e6, 1),
+            "roofline": {"bound": "hbm", "achieved": round(bpu * N / (sec / K) / 1e9, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(bpu * N / (sec / K) / 1e9 / peak, 4), "peak_kind": kind},
+            "mass_drift_rel": abs(m1 - m0) / m0, "momentum_x": p1[0]}
+
+
+def precision_line(args):
+    """Lid-driven cavity 768^3 (lid (0.1,0,0)), populations stored as f - w
+    in FP16 and BF16 with FP32 math, against the FP32 run of the same case:
+    max |u - u_f32| / max |u_f32| after K steps, mass drift from the FP64
+    reduction, MLUPS; plus the 64^3 copy against the FP64 oracle."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    from paper_2409_16781_gb300 import Lattice, LbDiverged
+    from paper_2409_16781_gb300 import workloads as W
+    n, K = 768, args.steps
+    flags = W.cavity_flags(n, n, n)
+    out = {"lattice": [n, n, n], "steps": K, "runs": []}
+    stream = torch.cuda.current_stream()
+
+    def run(storage, tau):
+        lat = Lattice(n, n, n, tau, u_lid=(0.1, 0, 0), flags=flags, storage=storage, stream=stream)
+        lat.autotune(reps=3, cache=False)
+        m0, _ = lat.totals()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        done, diverged = 0, None
+        e0.record(stream)
+        while done < K:
+            k = min(500, K - done)
+            lat.step(k)
+            done += k
+            try:
+                m1, _ = lat.totals()
+            except LbDiverged:
+                diverged = done
+                break
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        u = None if diverged else lat.moments_device()[1]
+        lat.close()
+        return u, (None if diverged else abs(m1 - m0) / m0), done * n ** 3 / sec / 1e6, diverged
+
+    for tau in [float(t) for t in args.taus.split(",")]:
+        u32, md32, ml32, dv32 = run("f32", tau)
+        rec = {"tau": tau, "f32": {"mlups": round(ml32, 1), "mass_drift": md32, "diverged_at": dv32}}
+        umax = None if u32 is None else u32.abs().max().item()
+        for storage in ("f16s", "bf16s"):
+            u, md, ml, dv = run(storage, tau)
+            err = None
+            if u is not None and u32 is not None:
+                err = (u - u32).abs().max().item() / umax
+            rec[storage] = {"mlups": round(ml, 1), "mass_drift": md, "u_err_vs_f32": err, "diverged_at": dv}
+            del u
+        del u32
+        torch.cuda.empty_cache()
+        out["runs"].append(rec)
+    # the 64^3 copy against the FP64 oracle
+    m = 64
+    fl = W.cavity_flags(m, m, m)
+    ora = O.Lattice(m, m, m, 0.6, u_lid=(0.1, 0, 0), flags=fl)
+    ora.step(min(K, 5000))
+    _, u_o = ora.moments()
+    mask = fl == 0
+    small = {"lattice": [m, m, m], "tau": 0.6, "steps": min(K, 5000)}
+    for storage in ("f32", "f16s", "bf16s"):
+        lat = Lattice(m, m, m, 0.6, u_lid=(0.1, 0, 0), flags=fl, storage=storage)
+        lat.step(min(K, 5000))
+        _, u_g = lat.moments()
+        lat.close()
+        small[storage] = float(np.abs(u_g[:, mask] - u_o[:, mask]).max() / np.abs(u_o[:, mask]).max())
+    out["vs_oracle_64"] = small
+    return {"metric": METRIC, "value": out["runs"][-1]["f16s"]["mlups"], "unit": "MLUPS", "n_gpus": 1,
+            "steps": K, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16", "data": "synthetic",
+            "config": {"workload": "cavity 768^3 precision study: f - w stored in FP16 / BF16, FP32 math, "
+                                   "vs the FP32 GPU run and the FP64 oracle at 64^3"},
+            "precision": out}
 
 
 def serve_line(args):
