@@ -149,9 +149,9 @@ int lb_get_populations_at(lb_lattice *h, const int64_t *cells, int n, double *ou
  * 2, 3 as 1 with streaming / L2-only cache policies; 4, 5 two cells per
  * thread (even nx); 6, 7 two cells per thread, packed 16-bit registers
  * (16-bit storage, even nx); 8, 9 four cells per thread, packed 16-bit
- * (16-bit storage, nx % 4 == 0); 10, 11 TMA bulk-copy pipeline through
- * shared memory, four / two cells per thread (16-bit storage, nx % 16 == 0;
- * block size fixed).  A variant that
+ * (16-bit storage, nx % 4 == 0); 10, 11, 12 TMA bulk-copy pipeline
+ * through shared memory, four / two / one cells per thread (16-bit storage,
+ * nx % 16 == 0; block size fixed).  A variant that
  * does not apply to the
  * lattice runs variant 1.  block = threads per block (0 = default; rounded
  * down to whole warps). */

@@ -403,7 +403,7 @@ int lb_get_populations_at(lb_lattice* h, const int64_t* cells, int n, double* ou
 
 int lb_set_kernel(lb_lattice* h, int variant, int block) {
     if (!h) return fail(LB_EINVAL, "lb_set_kernel: NULL handle");
-    if (variant < 0 || variant > 11 || block < 0 || block > 1024)
+    if (variant < 0 || variant > 12 || block < 0 || block > 1024)
         return fail(LB_EINVAL, "lb_set_kernel: bad variant %d / block %d", variant, block);
     h->kernel = variant;
     h->block = block;
@@ -432,6 +432,7 @@ int lb_autotune(lb_lattice* h, int reps, int* variant, int* block, float* ms_per
     if (sixteen && h->nx % 16 == 0) {
         add(10, 0);
         add(11, 0);
+        add(12, 0);
     }
     const LatticeParams p = params_of(h);
     cudaEvent_t e0, e1;

@@ -415,11 +415,14 @@ static cudaError_t step_rows_t(const void* A, void* B, const uint8_t* code, cons
 // waited (again bounded) for the copies it issued.
 // ---------------------------------------------------------------------------
 constexpr int TMA_STAGES = 4;
-constexpr int TMA_CONSUMER_WARPS = 4;
-constexpr int TMA_THREADS = 32 * (1 + TMA_CONSUMER_WARPS);
+// consumer warps per block and threads per block for G cells per consumer
+// thread: four-cell and two-cell threads use 4 consumer warps, one-cell
+// threads 8 (fewer registers each, so more warps hide shared-memory latency)
+__host__ __device__ constexpr int tma_consumer_warps(int G) { return G == 1 ? 8 : 4; }
+__host__ __device__ constexpr int tma_threads(int G) { return 32 * (1 + tma_consumer_warps(G)); }
 constexpr int TMA_HALO = 8;  // 16 bytes of 16-bit values
 // cells per tile with G cells per consumer thread
-__host__ __device__ constexpr int tma_tile_cells(int G) { return G * 32 * TMA_CONSUMER_WARPS; }
+__host__ __device__ constexpr int tma_tile_cells(int G) { return G * 32 * tma_consumer_warps(G); }
 // largest stage ring: TX = 16 -> R = tile/16 rows of 19 * (16 + 16) * 2 + 16 bytes
 __host__ __device__ constexpr int tma_max_smem(int G) {
     return TMA_STAGES * (tma_tile_cells(G) / 16) * (19 * (16 + 2 * TMA_HALO) * 2 + 16);
@@ -479,7 +482,7 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 }
 
 template <class S, bool FORCE, int G>
-__global__ void __launch_bounds__(TMA_THREADS, G == 4 ? 2 : 4) step_kernel_tma16(const S* __restrict__ A, S* __restrict__ B,
+__global__ void __launch_bounds__(tma_threads(G), G == 4 ? 2 : (G == 2 ? 4 : 3)) step_kernel_tma16(const S* __restrict__ A, S* __restrict__ B,
                                                                  const uint8_t* __restrict__ code, LatticeParams p,
                                                                  TmaGeom g) {
     static_assert(sizeof(S) == 2, "16-bit storage only");
@@ -492,7 +495,7 @@ __global__ void __launch_bounds__(TMA_THREADS, G == 4 ? 2 : 4) step_kernel_tma16
     if (threadIdx.x == 0) {
         for (int s = 0; s < TMA_STAGES; ++s) {
             mbar_init(smem_addr(&full_bar[s]), 1);
-            mbar_init(smem_addr(&empty_bar[s]), TMA_CONSUMER_WARPS);
+            mbar_init(smem_addr(&empty_bar[s]), tma_consumer_warps(G));
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -561,10 +564,11 @@ __global__ void __launch_bounds__(TMA_THREADS, G == 4 ? 2 : 4) step_kernel_tma16
     }
 
     // -------------------------------- consumers --------------------------------
-    const int ct = (warp - 1) * 32 + lane;  // 0 .. 127
+    const int ct = (warp - 1) * 32 + lane;  // 0 .. 32 * consumer warps - 1
     const int groups_per_row = g.TX / G;
     const int r = ct / groups_per_row, j = ct % groups_per_row;
-    using W = typename std::conditional<G == 4, uint2, uint32_t>::type;  // G packed 16-bit values
+    // G packed 16-bit values per direction
+    using W = typename std::conditional<G == 4, uint2, typename std::conditional<G == 2, uint32_t, uint16_t>::type>::type;
     int64_t k = 0;
     for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x, ++k) {
         const int s = (int)(k % TMA_STAGES);
@@ -593,7 +597,9 @@ __global__ void __launch_bounds__(TMA_THREADS, G == 4 ? 2 : 4) step_kernel_tma16
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const uint8_t* b = rb8 + i * g.rb + 2 * (TMA_HALO + G * j);
-            if constexpr (G == 4) {
+            if constexpr (G == 1) {
+                v[i] = *reinterpret_cast<const uint16_t*>(b - 2 * D3Q19::cx(i));  // the value at x - c_x
+            } else if constexpr (G == 4) {
                 const uint2 q = *reinterpret_cast<const uint2*>(b);
                 if (D3Q19::cx(i) == 0) {
                     v[i] = q;
@@ -617,8 +623,10 @@ __global__ void __launch_bounds__(TMA_THREADS, G == 4 ? 2 : 4) step_kernel_tma16
         }
         if constexpr (G == 4)
             codes = *reinterpret_cast<const uint32_t*>(rb8 + 19 * g.rb + 4 * j);
-        else
+        else if constexpr (G == 2)
             codes = *reinterpret_cast<const uint16_t*>(rb8 + 19 * g.rb + 2 * j);
+        else
+            codes = rb8[19 * g.rb + j];
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_addr(&empty_bar[s]));  // this warp's shared-memory reads are done
         if (!mine) continue;
@@ -630,7 +638,7 @@ __global__ void __launch_bounds__(TMA_THREADS, G == 4 ? 2 : 4) step_kernel_tma16
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             if constexpr (G == 4) out[i] = make_uint2(0u, 0u);
-            else out[i] = 0u;
+            else out[i] = 0;
         }
 #pragma unroll
         for (int kk = 0; kk < G; ++kk) {
@@ -638,7 +646,8 @@ __global__ void __launch_bounds__(TMA_THREADS, G == 4 ? 2 : 4) step_kernel_tma16
 #pragma unroll
             for (int i = 0; i < Q; ++i) {
                 if constexpr (G == 4) d[i] = get16<S>(v[i], kk);
-                else d[i] = kk == 0 ? lo16<S>(v[i]) : hi16<S>(v[i]);
+                else if constexpr (G == 2) d[i] = kk == 0 ? lo16<S>(v[i]) : hi16<S>(v[i]);
+                else d[i] = lo16<S>((uint32_t)v[i]);
             }
             const uint8_t ck = (uint8_t)(codes >> (8 * kk));
             if (ck & CODE_NEAR_WALL) bounce_fix<S, 0>(A, code, p, xq + kk, y, z, cell0 + kk, d);
@@ -650,12 +659,12 @@ __global__ void __launch_bounds__(TMA_THREADS, G == 4 ? 2 : 4) step_kernel_tma16
                     if (kk < 2) out[i].x |= h;
                     else out[i].y |= h;
                 } else {
-                    out[i] |= h;
+                    out[i] |= (W)h;
                 }
             }
         }
         uint16_t* B16 = reinterpret_cast<uint16_t*>(B);
-        const uint32_t solid_mask = G == 4 ? 0x03030303u : 0x0303u;
+        const uint32_t solid_mask = G == 4 ? 0x03030303u : (G == 2 ? 0x0303u : 0x03u);
         if ((codes & solid_mask) == 0) {
 #pragma unroll
             for (int i = 0; i < Q; ++i) *reinterpret_cast<W*>(B16 + (int64_t)i * p.ps + cell0) = out[i];
@@ -725,7 +734,7 @@ static cudaError_t launch_tma16(const void* A, void* B, const uint8_t* code, con
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tma_max_smem(G))) != cudaSuccess)
             return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TMA_THREADS, smem)) != cudaSuccess)
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tma_threads(G), smem)) != cudaSuccess)
             return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         cache[ncache % 8] = Shape{dev, smem, sms, per_sm};
@@ -733,7 +742,7 @@ static cudaError_t launch_tma16(const void* A, void* B, const uint8_t* code, con
     }
     int64_t grid = (int64_t)sms * per_sm;
     if (grid > g.ntiles) grid = g.ntiles;
-    kern<<<(unsigned)grid, TMA_THREADS, smem, st>>>((const S*)A, (S*)B, code, p, g);
+    kern<<<(unsigned)grid, tma_threads(G), smem, st>>>((const S*)A, (S*)B, code, p, g);
     return cudaGetLastError();
 }
 
@@ -795,9 +804,11 @@ static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* co
             return step_rows_t<S, 0>(A, B, code, p, block, st);
         case 10:
         case 11:
+        case 12:
             if constexpr (sizeof(S) == 2)
                 return variant == 10 ? step_tma16_t<S, 4>(A, B, code, p, block, st)
-                                     : step_tma16_t<S, 2>(A, B, code, p, block, st);
+                       : variant == 11 ? step_tma16_t<S, 2>(A, B, code, p, block, st)
+                                       : step_tma16_t<S, 1>(A, B, code, p, block, st);
             return step_rows_t<S, 0>(A, B, code, p, block, st);
         case 0:
             // measured defaults on GB300 (256^3): FP32 one cell per thread in

@@ -91,7 +91,7 @@ def test_tiny_grids(case, storage, kernel, perm):
     check_pair(ora, gpu, storage, perm, flags)
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12])
 @pytest.mark.parametrize("storage", STORAGES)
 def test_every_variant(storage, kernel, perm):
     """Every step-kernel variant (cache policies, one or two cells per
@@ -235,7 +235,7 @@ def test_autotune_keeps_state(storage, perm, tmp_path, monkeypatch):
 @pytest.mark.parametrize("storage", ["f16s", "bf16s"])
 @pytest.mark.parametrize("dims", [(32, 6, 5), (48, 5, 3), (64, 3, 4), (96, 5, 3), (512, 3, 2), (256, 4, 3)],
                          ids=lambda d: "x".join(map(str, d)))
-@pytest.mark.parametrize("kernel", [10, 11])
+@pytest.mark.parametrize("kernel", [10, 11, 12])
 def test_tma_pipeline_variant(dims, storage, kernel, perm):
     """Variant 10 (bulk copies into a shared-memory ring): tile widths 16..512
     cells, partial last tiles, walls, lid and force, several steps."""
