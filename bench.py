@@ -35,7 +35,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "D3Q19 MLUPS & fraction of HBM roofline; batched-serve p50/p99 vs plain FP32 launches"
-STORAGE_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2}
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2, "f32d": 4}
 FALLBACK_HBM_GBS = 6800.0
 # the files that make up the step kernel (hashed to tie ncu figures to it)
 STEP_SOURCES = ("lb_common.cuh", "lb_kernels.cuh", "lb_step.cu")
@@ -327,7 +327,7 @@ def run_ours(args, dist: Dist):
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": dist.world,
         "steps": K, "warmup": args.warmup, "ms_per_step": round(t_max * 1e3 / K, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"f64": "f64", "f32": "f32", "f16s": "f16", "bf16s": "bf16"}[args.storage],
+        "dtype": {"f64": "f64", "f32": "f32", "f16s": "f16", "bf16s": "bf16", "f32d": "f32+f64"}[args.storage],
         "data": "synthetic",
         "config": {"workload": f"taylor-green vortex {n}^3, D3Q19 BGK, {args.storage} populations "
                                f"(f - w), tau={tau}, u0=0.05, k=2pi/{n}",
@@ -374,6 +374,7 @@ def run_serving(n_requests, rate_multipliers=(2.0,), budget_gb=64.0, seed=16781,
            "policy": "batched: shortest remaining work first, 4M-cell occupancy target, 8 ms chunks, "
                      "3 queued; sequential: FIFO, one lattice at a time, one launch per step",
            "runs": []}
+    out["f16s_accuracy"] = f16s_accuracy(base, samples=6, device=device)
     for mult in rate_multipliers:
         reqs = W.request_stream(n=n_requests, rate_hz=mult * capacity, seed=seed)
         be = BatchBackend(int(budget_gb * (1 << 30)), max_slots=1024, device=device)
@@ -385,6 +386,33 @@ def run_serving(n_requests, rate_multipliers=(2.0,), budget_gb=64.0, seed=16781,
         out["runs"].append({"rate_multiplier": mult, "rate_hz": round(mult * capacity, 3),
                             "batched": sb.summary(), "sequential_fp32": ss.summary()})
     return out
+
+
+def f16s_accuracy(requests, samples=6, device=None):
+    """Velocity error of served FP16-storage requests: each sampled request
+    (the largest cells x steps first, then every other) runs alone in FP16S
+    and in FP32; max |u16 - u32| / max |u32| over fluid cells."""
+    from paper_2409_16781_gb300 import Lattice
+    cand = sorted([r for r in requests if r.storage == "f16s"], key=lambda r: -r.cells * r.steps)
+    pick = cand[:samples // 2] + cand[samples // 2::max(1, len(cand) // max(1, samples - samples // 2))]
+    pick = pick[:samples]
+    errs = []
+    for r in pick:
+        u = {}
+        for storage in ("f32", "f16s"):
+            lat = Lattice(r.nx, r.ny, r.nz, r.tau, u_lid=r.u_lid, flags=r.flags(), storage=storage,
+                          force=r.force, device=device)
+            lat.step(r.steps)
+            u[storage] = lat.moments()[1]
+            lat.close()
+        mask = r.flags() == 0
+        ref = u["f32"][:, mask]
+        errs.append(float(abs(u["f16s"][:, mask] - ref).max() / max(abs(ref).max(), 1e-30)))
+    return {"sampled": len(errs), "max_err": max(errs) if errs else None,
+            "median_err": sorted(errs)[len(errs) // 2] if errs else None,
+            "within_2e-3": sum(e <= 2e-3 for e in errs),
+            "cases": [{"dims": [r.nx, r.ny, r.nz], "tau": round(r.tau, 3), "steps": r.steps, "kind": r.kind,
+                       "err": e} for r, e in zip(pick, errs)]}
 
 
 # ---------------------------------------------------------------- oracle

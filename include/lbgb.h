@@ -53,14 +53,15 @@ typedef enum {
     LB_EBUSY = -6      /* resource in use (batch capacity reached) */
 } lb_status;
 
-/* Population storage (the paper's precision modes, Sec. 3.1.1).  The "S"
- * forms store the deviation f_i - w_i; all math is FP32 except LB_F64,
- * which stores and computes in FP64.  LB_F32 also stores f_i - w_i. */
+/* Population storage (the paper's precision modes, Sec. 3.1.1).  Every
+ * form stores the deviation f_i - w_i; the math is FP32 except for LB_F64
+ * (FP64 storage and math) and LB_F32D (FP32 storage, FP64 math). */
 typedef enum {
     LB_F64 = 0,   /* "Double": FP64 storage, FP64 math            */
     LB_F32 = 1,   /* "Single": FP32 storage, FP32 math            */
     LB_F16S = 2,  /* "Mixed1": FP16 storage of f - w, FP32 math   */
-    LB_BF16S = 3  /* BF16 storage of f - w, FP32 math             */
+    LB_BF16S = 3, /* BF16 storage of f - w, FP32 math             */
+    LB_F32D = 4   /* "Mixed2": FP32 storage of f - w, FP64 math   */
 } lb_storage;
 
 /* Cell flags (uint8 per cell). */

@@ -141,7 +141,7 @@ int create_common(lb_lattice** out, int nx, int ny, int nz, double tau, const do
     lb_options o = opt ? *opt : defaults();
     if (!valid_dims(nx, ny, nz)) return fail(LB_EINVAL, "lb_create: bad dims %d x %d x %d", nx, ny, nz);
     if (!(tau > 0.5) || !std::isfinite(tau)) return fail(LB_EINVAL, "lb_create: tau must be > 1/2 (got %g)", tau);
-    if (o.storage < LB_F64 || o.storage > LB_BF16S) return fail(LB_EINVAL, "lb_create: bad storage %d", o.storage);
+    if (o.storage < LB_F64 || o.storage > LB_F32D) return fail(LB_EINVAL, "lb_create: bad storage %d", o.storage);
     for (int a = 0; a < 3; ++a) {
         if (!std::isfinite(o.force[a])) return fail(LB_EINVAL, "lb_create: non-finite force");
         if (u_lid && !std::isfinite(u_lid[a])) return fail(LB_EINVAL, "lb_create: non-finite u_lid");
@@ -247,7 +247,7 @@ int lb_velocity_set(int* c, double* w) {
 
 size_t lb_bytes_required(int nx, int ny, int nz, const lb_options* opt) {
     const int storage = opt ? opt->storage : LB_F32;
-    if (!valid_dims(nx, ny, nz) || storage < LB_F64 || storage > LB_BF16S) return 0;
+    if (!valid_dims(nx, ny, nz) || storage < LB_F64 || storage > LB_F32D) return 0;
     return layout_for(nx, ny, nz, storage).total;
 }
 

@@ -26,7 +26,7 @@ namespace lbgb {
 namespace {
 
 constexpr int BATCH_THREADS = 128;   // cells per work item = threads per block
-constexpr int BATCH_TYPES = 4;       // storage types
+constexpr int BATCH_TYPES = 5;       // storage types
 constexpr int GRAPH_STEPS = 8;       // batched steps per captured graph
 constexpr size_t BALIGN = 256;
 
@@ -287,7 +287,7 @@ struct lb_batch {
     cudaEvent_t up_ev[NUP] = {};
     int up_next = 0;
     bool dirty = true;
-    int grid[BATCH_TYPES] = {0, 0, 0, 0};
+    int grid[BATCH_TYPES] = {0, 0, 0, 0, 0};
     cudaGraphExec_t graph = nullptr;
 };
 
@@ -437,9 +437,13 @@ cudaError_t launch_type(lb_batch* b, int t, cudaStream_t st) {
             batch_step_kernel<__half><<<grid, BATCH_THREADS, 0, st>>>(b->d_slots, b->d_parity, b->d_remaining,
                                                                       b->d_act[2], b->d_off[2], b->d_nact + 2);
             break;
-        default:
+        case 3:
             batch_step_kernel<__nv_bfloat16><<<grid, BATCH_THREADS, 0, st>>>(
                 b->d_slots, b->d_parity, b->d_remaining, b->d_act[3], b->d_off[3], b->d_nact + 3);
+            break;
+        default:
+            batch_step_kernel<f32d><<<grid, BATCH_THREADS, 0, st>>>(b->d_slots, b->d_parity, b->d_remaining,
+                                                                    b->d_act[4], b->d_off[4], b->d_nact + 4);
             break;
     }
     return cudaGetLastError();
@@ -603,7 +607,7 @@ int batch_create_common(lb_batch** out, size_t capacity, int max_slots, void* st
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) {
-        int per[BATCH_TYPES] = {0, 0, 0, 0};
+        int per[BATCH_TYPES] = {0, 0, 0, 0, 0};
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], batch_step_kernel<double>, BATCH_THREADS, 0);
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], batch_step_kernel<float>, BATCH_THREADS, 0);
@@ -612,6 +616,8 @@ int batch_create_common(lb_batch** out, size_t capacity, int max_slots, void* st
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[3], batch_step_kernel<__nv_bfloat16>, BATCH_THREADS,
                                                               0);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[4], batch_step_kernel<f32d>, BATCH_THREADS, 0);
         for (int t = 0; t < BATCH_TYPES; ++t) b->grid[t] = sms * (per[t] > 0 ? per[t] : 1);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -650,7 +656,7 @@ extern "C" {
 
 size_t lb_batch_slot_bytes(int nx, int ny, int nz, int storage) {
     if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz >= (int64_t(1) << 31)) return 0;
-    if (storage < LB_F64 || storage > LB_BF16S) return 0;
+    if (storage < LB_F64 || storage > LB_F32D) return 0;
     return slot_bytes(nx, ny, nz, storage);
 }
 
@@ -678,7 +684,7 @@ int lb_batch_add(lb_batch* b, int nx, int ny, int nz, double tau, const double* 
     if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz >= (int64_t(1) << 31))
         return bfail(LB_EINVAL, "lb_batch_add: bad dims %d x %d x %d", nx, ny, nz);
     if (!(tau > 0.5) || !std::isfinite(tau)) return bfail(LB_EINVAL, "lb_batch_add: tau must be > 1/2");
-    if (o.storage < LB_F64 || o.storage > LB_BF16S) return bfail(LB_EINVAL, "lb_batch_add: bad storage");
+    if (o.storage < LB_F64 || o.storage > LB_F32D) return bfail(LB_EINVAL, "lb_batch_add: bad storage");
     if (steps < 0) return bfail(LB_EINVAL, "lb_batch_add: steps < 0");
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(o.force[a]) || (u_lid && !std::isfinite(u_lid[a])))

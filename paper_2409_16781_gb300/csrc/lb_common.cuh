@@ -82,6 +82,18 @@ template <> struct Storage<__nv_bfloat16> {
     __device__ __forceinline__ static __nv_bfloat16 store(float v) { return __float2bfloat16_rn(v); }
 };
 
+// "Mixed2" (the paper's Sec. 3.1.1): FP32 storage, FP64 arithmetic.  A
+// distinct 4-byte type so that the templates can tell it from FP32 math.
+struct f32d {
+    float v;
+};
+template <> struct Storage<f32d> {
+    using math = double;
+    static constexpr int id = 4;
+    __device__ __forceinline__ static double load(f32d v) { return (double)v.v; }
+    __device__ __forceinline__ static f32d store(double v) { return f32d{__double2float_rn(v)}; }
+};
+
 // Parameters of one lattice as seen by the kernels.
 struct LatticeParams {
     int nx, ny, nz;

@@ -33,6 +33,7 @@ cudaError_t launch_gather_pops(int storage, const void* A, int64_t ps, const int
         case 1: { using S = float; return CALL; }         \
         case 2: { using S = __half; return CALL; }        \
         case 3: { using S = __nv_bfloat16; return CALL; } \
+        case 4: { using S = f32d; return CALL; }          \
         default: return cudaErrorInvalidValue;            \
     }
 
@@ -42,6 +43,7 @@ inline int storage_bytes(int storage) {
         case 1: return 4;
         case 2: return 2;
         case 3: return 2;
+        case 4: return 4;
         default: return 0;
     }
 }

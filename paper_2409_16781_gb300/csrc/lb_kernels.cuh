@@ -8,6 +8,8 @@
 // Sec. 3.3 (lid-driven cavity: no-slip walls and a lid moving at u0).
 #pragma once
 
+#include <type_traits>
+
 #include "lb_common.cuh"
 
 namespace lbgb {
@@ -17,14 +19,22 @@ namespace lbgb {
 //   HINT 2: L2 only for loads (.cg), streaming stores.
 template <int HINT, class S>
 __device__ __forceinline__ S ld_pop(const S* p) {
-    if constexpr (HINT == 1) return __ldcs(p);
-    else if constexpr (HINT == 2) return __ldcg(p);
-    else return *p;
+    if constexpr (std::is_same<S, f32d>::value) {
+        return f32d{ld_pop<HINT>(reinterpret_cast<const float*>(p))};
+    } else {
+        if constexpr (HINT == 1) return __ldcs(p);
+        else if constexpr (HINT == 2) return __ldcg(p);
+        else return *p;
+    }
 }
 template <int HINT, class S>
 __device__ __forceinline__ void st_pop(S* p, S v) {
-    if constexpr (HINT == 0) *p = v;
-    else __stcs(p, v);
+    if constexpr (std::is_same<S, f32d>::value) {
+        st_pop<HINT>(reinterpret_cast<float*>(p), v.v);
+    } else {
+        if constexpr (HINT == 0) *p = v;
+        else __stcs(p, v);
+    }
 }
 
 // Streaming, pull form: d[i] <- A_i(x - c_i), with periodic wrap at the

@@ -777,15 +777,21 @@ static cudaError_t step_rows_t(const void* A, void* B, const uint8_t* code, cons
 template <class S>
 static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* code, const LatticeParams& p,
                           int block, cudaStream_t st) {
-    const bool pairs_ok = (p.nx % 2) == 0;
+    // the two-cell FP32/FP64 kernels have no FP32-storage/FP64-math form
+    const bool pairs_ok = (p.nx % 2) == 0 && !std::is_same<S, f32d>::value;
     switch (variant) {
         case 1: return step_rows_t<S, 0>(A, B, code, p, block, st);
         case 2: return step_rows_t<S, 1>(A, B, code, p, block, st);
         case 3: return step_rows_t<S, 2>(A, B, code, p, block, st);
         case 4:
-            return pairs_ok ? step_pairs_t<S, 0>(A, B, code, p, block, st) : step_rows_t<S, 0>(A, B, code, p, block, st);
         case 5:
-            return pairs_ok ? step_pairs_t<S, 1>(A, B, code, p, block, st) : step_rows_t<S, 1>(A, B, code, p, block, st);
+            if constexpr (!std::is_same<S, f32d>::value) {
+                if (pairs_ok)
+                    return variant == 4 ? step_pairs_t<S, 0>(A, B, code, p, block, st)
+                                        : step_pairs_t<S, 1>(A, B, code, p, block, st);
+            }
+            return variant == 4 ? step_rows_t<S, 0>(A, B, code, p, block, st)
+                                : step_rows_t<S, 1>(A, B, code, p, block, st);
         case 6:
         case 7:
             if constexpr (sizeof(S) == 2) {

@@ -23,7 +23,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 
-BYTES_PER_UPDATE = {"f64": 305, "f32": 153, "f16s": 77, "bf16s": 77}
+BYTES_PER_UPDATE = {"f64": 305, "f32": 153, "f16s": 77, "bf16s": 77, "f32d": 153}
 
 
 @dataclass

@@ -21,10 +21,10 @@ from paper_2409_16781_gb300.serve import BatchBackend, SequentialBackend, serve
 
 pytestmark = pytest.mark.gpu
 
-VEL_TOL = {"f32": 1e-5, "f16s": 2e-3, "bf16s": 3e-2}
+VEL_TOL = {"f32": 1e-5, "f16s": 2e-3, "bf16s": 3e-2, "f32d": 1e-6}
 # relative mass agreement: the storage rounding of each deviation bounds how
 # closely two kernels' conserved sums agree (16-bit: about one ulp per cell)
-MASS_TOL = {"f64": 1e-12, "f32": 1e-8, "f16s": 1e-5, "bf16s": 1e-4}
+MASS_TOL = {"f64": 1e-12, "f32": 1e-8, "f16s": 1e-5, "bf16s": 1e-4, "f32d": 1e-8}
 
 MIX = [
     # nx, ny, nz, tau, storage, kind, steps
@@ -35,6 +35,7 @@ MIX = [
     (24, 24, 24, 0.52, "f32", "channel", 57),
     (5, 31, 6, 0.8, "f16s", "cavity", 11),
     (64, 3, 2, 0.65, "f32", "random", 21),
+    (15, 11, 7, 0.75, "f32d", "cavity", 19),
 ]
 
 
