@@ -15,7 +15,9 @@ Parity pins: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_pins.py`` (lattice isotropy, equilibrium and source moment
 closed forms, rest fixed point, pure-streaming transport, conservation laws,
 shear-wave and Taylor-Green decay rates, Couette and Poiseuille steady
-profiles, Galilean advection, mirror symmetry, and a brute-force push stepper).
+profiles, Galilean advection, mirror symmetry, and a brute-force push stepper;
+for the TRT collision: reduction to BGK, conservation, Lambda-independent
+viscosity, and the exact Poiseuille parabola at Lambda = 3/16 for any tau).
 """
 from __future__ import annotations
 
@@ -70,7 +72,15 @@ def load_library(path: str):
     lib.lbo_run.restype = I
     lib.lbo_moments.argtypes = [I, I, I, P, P, P, P, P, P]
     lib.lbo_totals.argtypes = [I, I, I, P, P, P, P, P]
+    lib.lbo_step_trt.argtypes = [I, I, I, D, D, P, P, P, P, P]
+    lib.lbo_run_trt.argtypes = [I, I, I, D, D, P, P, P, P, P, I]
+    lib.lbo_run_trt.restype = I
     return lib
+
+
+def trt_omega_minus(tau: float, magic: float = 3.0 / 16.0) -> float:
+    """omega- from the TRT parameter Lambda = (1/omega+ - 1/2)(1/omega- - 1/2)."""
+    return 1.0 / (magic / (tau - 0.5) + 0.5)
 
 
 def _load():
@@ -138,8 +148,10 @@ class Lattice:
     (19, nz, ny, nx) in the oracle's velocity order, plus a scratch ``B``."""
 
     def __init__(self, nx, ny, nz, tau, u_lid=(0.0, 0.0, 0.0), flags=None,
-                 force=(0.0, 0.0, 0.0), lib=None):
+                 force=(0.0, 0.0, 0.0), lib=None, omega_minus=None):
+        """omega_minus: None = BGK; otherwise the TRT odd-part rate."""
         self.lib = _lib_or_default(lib)
+        self.omega_minus = None if omega_minus is None else float(omega_minus)
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.N = self.nx * self.ny * self.nz
         self.tau = float(tau)
@@ -168,9 +180,14 @@ class Lattice:
         n = int(n)
         if n <= 0:
             return
-        which = self.lib.lbo_run(self.nx, self.ny, self.nz, self.tau, _ptr(self.u_lid),
-                                 _ptr(self.g), _ptr(self.flags), _ptr(self.A),
-                                 _ptr(self.B), n)
+        if self.omega_minus is None:
+            which = self.lib.lbo_run(self.nx, self.ny, self.nz, self.tau, _ptr(self.u_lid),
+                                     _ptr(self.g), _ptr(self.flags), _ptr(self.A),
+                                     _ptr(self.B), n)
+        else:
+            which = self.lib.lbo_run_trt(self.nx, self.ny, self.nz, self.tau, self.omega_minus,
+                                         _ptr(self.u_lid), _ptr(self.g), _ptr(self.flags),
+                                         _ptr(self.A), _ptr(self.B), n)
         if which == 1:
             self.A, self.B = self.B, self.A
 
@@ -190,13 +207,17 @@ class Lattice:
         return float(out[0]), out[1:].copy()
 
 
-def step_array(nx, ny, nz, tau, u_lid, force, flags, A, lib=None):
+def step_array(nx, ny, nz, tau, u_lid, force, flags, A, lib=None, omega_minus=None):
     """One step on a caller-supplied array A (19*N float64, oracle order);
     returns the new post-collision array (solid cells copied from A)."""
     lib = _lib_or_default(lib)
     A = _f64(A, (Q * nx * ny * nz,))
     B = A.copy()
     fl = _flags(flags, nx * ny * nz)
-    lib.lbo_step(int(nx), int(ny), int(nz), float(tau), _ptr(_f64(u_lid, (3,))),
-                 _ptr(_f64(force, (3,))), _ptr(fl), _ptr(A), _ptr(B))
+    if omega_minus is None:
+        lib.lbo_step(int(nx), int(ny), int(nz), float(tau), _ptr(_f64(u_lid, (3,))),
+                     _ptr(_f64(force, (3,))), _ptr(fl), _ptr(A), _ptr(B))
+    else:
+        lib.lbo_step_trt(int(nx), int(ny), int(nz), float(tau), float(omega_minus),
+                         _ptr(_f64(u_lid, (3,))), _ptr(_f64(force, (3,))), _ptr(fl), _ptr(A), _ptr(B))
     return B

@@ -34,6 +34,13 @@
  *
  * Array layout used by this file: f[q * N + cell], cell = x + nx*(y + ny*z),
  * q in this file's own velocity order (lbo_velocity_set reports it).
+ *
+ * Two-relaxation-time collision (not in the paper; an alternative collision
+ * for tau near 1/2, Ginzburg's TRT): lbo_step_trt relaxes the part of each
+ * population even under c -> -c, f+_i = (f_i + f_opp(i))/2, with omega+ =
+ * 1/tau and the odd part f-_i = (f_i - f_opp(i))/2 with omega-; the Guo
+ * source splits the same way, its even part scaled by (1 - omega+/2) and its
+ * odd part by (1 - omega-/2).  omega- = omega+ is BGK.
  */
 #include <stddef.h>
 #include <stdint.h>
@@ -198,6 +205,61 @@ void lbo_step(int nx, int ny, int nz, double tau, const double *ulid, const doub
                 for (int i = 0; i < LBO_Q; ++i)                         /* Eq. 1 */
                     B[(size_t)i * N + cell] = f[i] - omega * (f[i] - feq[i]) + S[i];
             }
+}
+
+/* Unscaled Guo term G_i = w_i [3(c_i - u) + 9 (c_i.u) c_i] . F, F = rho g. */
+static void lbo_guo_unscaled(double rho, const double *u, const double *g, double *G)
+{
+    double F[3] = {rho * g[0], rho * g[1], rho * g[2]};
+    for (int i = 0; i < LBO_Q; ++i) {
+        double cu = lbo_c[i][0] * u[0] + lbo_c[i][1] * u[1] + lbo_c[i][2] * u[2];
+        double s = 0.0;
+        for (int a = 0; a < 3; ++a)
+            s += (3.0 * (lbo_c[i][a] - u[a]) + 9.0 * cu * lbo_c[i][a]) * F[a];
+        G[i] = lbo_w[i] * s;
+    }
+}
+
+/* One fused pull step with the TRT collision (omega+ = 1/tau, omega-). */
+void lbo_step_trt(int nx, int ny, int nz, double tau, double omega_minus, const double *ulid,
+                  const double *g, const uint8_t *flags, const double *A, double *B)
+{
+    lbo_build();
+    size_t N = (size_t)nx * ny * nz;
+    double wp = 1.0 / tau, wm = omega_minus;
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t cell = lbo_idx(x, y, z, nx, ny);
+                if (flags && flags[cell] != LBO_FLUID) continue;
+                double f[LBO_Q], feq[LBO_Q], G[LBO_Q], rho, u[3];
+                lbo_pull(nx, ny, nz, ulid, flags, A, x, y, z, f);
+                lbo_macro(f, g, &rho, u);
+                lbo_equilibrium(rho, u, feq);
+                lbo_guo_unscaled(rho, u, g, G);
+                for (int i = 0; i < LBO_Q; ++i) {
+                    int o = lbo_opp[i];
+                    double fp = 0.5 * (f[i] + f[o]), fm = 0.5 * (f[i] - f[o]);
+                    double ep = 0.5 * (feq[i] + feq[o]), em = 0.5 * (feq[i] - feq[o]);
+                    double gp = 0.5 * (G[i] + G[o]), gm = 0.5 * (G[i] - G[o]);
+                    B[(size_t)i * N + cell] = f[i] - wp * (fp - ep) - wm * (fm - em)
+                                              + (1.0 - 0.5 * wp) * gp + (1.0 - 0.5 * wm) * gm;
+                }
+            }
+}
+
+/* As lbo_run, with the TRT collision. */
+int lbo_run_trt(int nx, int ny, int nz, double tau, double omega_minus, const double *ulid,
+                const double *g, const uint8_t *flags, double *A, double *B, int n)
+{
+    for (int t = 0; t < n; ++t) {
+        if (t % 2 == 0)
+            lbo_step_trt(nx, ny, nz, tau, omega_minus, ulid, g, flags, A, B);
+        else
+            lbo_step_trt(nx, ny, nz, tau, omega_minus, ulid, g, flags, B, A);
+    }
+    return n % 2;
 }
 
 /* Run n steps starting from A, alternating A and B; returns the array that

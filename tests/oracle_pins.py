@@ -377,6 +377,113 @@ def pin_brute_force(lib=None):
                     f"brute force disagrees at {(x, y, z)} dir {c[i]}"
 
 
+# ------------------------------------------------------------------ TRT
+def pin_trt_reduces_to_bgk(lib=None):
+    """TRT with omega- = omega+ is the BGK step (to rounding) on a grid with
+    walls, lid and force."""
+    nx, ny, nz = 7, 6, 5
+    fl = W.random_flags(nx, ny, nz, seed=41, p_wall=0.2, p_lid=0.1)
+    _, w = O.velocity_set(lib)
+    A = W.random_populations(nx, ny, nz, seed=42, w=w, amp=0.02)
+    tau, ulid, g = 0.7, (0.03, -0.02, 0.01), (1e-4, 0.0, -2e-4)
+    b = O.step_array(nx, ny, nz, tau, ulid, g, fl, A, lib=lib)
+    t = O.step_array(nx, ny, nz, tau, ulid, g, fl, A, lib=lib, omega_minus=1.0 / tau)
+    assert np.abs(b - t).max() < 1e-16
+
+
+def pin_trt_single_cell(lib=None):
+    """TRT on a 1x1x1 periodic lattice (the collision alone) relaxes even
+    moments at omega+ and odd ones at omega-.  Closed forms for D3Q19 with
+    Guo forcing (F = rho g, u = j/rho + g/2): rho' = rho, j' = j + F,
+    Pi' = (1-w+) Pi + w+ rho (I/3 + uu) + (1-w+/2)(uF + Fu), and the odd
+    third moment Q_xyy = sum_i f_i c_ix c_iy^2, whose equilibrium value is
+    rho u_x / 3 and whose forcing value is F_x / 3:
+    Q' = (1-w-) Q + w- rho u_x / 3 + (1-w-/2) F_x / 3."""
+    c, w = O.velocity_set(lib)
+    cf = c.astype(np.float64)
+    rng = np.random.default_rng(17)
+    for _ in range(10):
+        tau = 0.51 + 1.5 * rng.random()
+        wp, wm = 1.0 / tau, 0.2 + 1.7 * rng.random()
+        g = 1e-3 * (rng.random(3) - 0.5)
+        f = w + 0.01 * (rng.random(19) - 0.5)
+        L = O.Lattice(1, 1, 1, tau, force=g, lib=lib, omega_minus=wm)
+        L.set_populations(f.reshape(19, 1, 1, 1))
+        L.step(1)
+        fp = L.A.reshape(19)
+        rho = f.sum()
+        j = f @ cf
+        u = j / rho + g / 2
+        F = rho * g
+        assert abs(fp.sum() - rho) < 1e-15
+        assert np.abs(fp @ cf - (j + F)).max() < 1e-16
+        Pi = np.einsum("i,ia,ib->ab", f, cf, cf)
+        Pi_p = np.einsum("i,ia,ib->ab", fp, cf, cf)
+        expect = ((1 - wp) * Pi + wp * rho * (I3 / 3 + np.outer(u, u))
+                  + (1 - wp / 2) * (np.outer(u, F) + np.outer(F, u)))
+        assert np.abs(Pi_p - expect).max() < 1e-15
+        phi = cf[:, 0] * cf[:, 1] ** 2
+        Q, Qp = f @ phi, fp @ phi
+        assert abs(Qp - ((1 - wm) * Q + wm * rho * u[0] / 3 + (1 - wm / 2) * F[0] / 3)) < 1e-16
+
+
+def pin_trt_conservation(lib=None):
+    """TRT conserves mass, and momentum grows by exactly mass * g per step in
+    a periodic box, whatever omega- is."""
+    nx, ny, nz = 8, 7, 6
+    rho, u = W.random_fields(nx, ny, nz, seed=43, du=0.04, drho=0.02)
+    g = np.array([2e-5, -1e-5, 3e-5])
+    L = O.Lattice(nx, ny, nz, 0.6, force=g, lib=lib, omega_minus=1.3)
+    L.init_fields(rho, u)
+    m0, p0 = L.totals()
+    L.step(30)
+    m1, p1 = L.totals()
+    assert abs(m1 - m0) < 1e-13 * m0
+    assert np.abs(p1 - (p0 + 30 * m0 * g)).max() < 1e-12 * m0 * np.abs(g).max() * 30
+
+
+def pin_trt_viscosity(lib=None):
+    """The shear viscosity is (tau - 1/2)/3 whatever Lambda is: the decay of
+    u0 sin(kz) with two different omega- agrees with nu to second order."""
+    n, tau = 64, 0.8
+    nu = (tau - 0.5) / 3
+    k = 2 * math.pi / n
+    z = np.arange(n)
+    for wm in (O.trt_omega_minus(tau, 3.0 / 16.0), O.trt_omega_minus(tau, 1.0 / 4.0)):
+        u = np.zeros((3, n, 1, 1))
+        u[0, :, 0, 0] = 1e-3 * np.sin(k * z)
+        L = O.Lattice(1, 1, n, tau, lib=lib, omega_minus=wm)
+        L.init_fields(None, u)
+        ts, amps = [], []
+        for t in range(0, 2001, 100):
+            _, uu = L.moments()
+            if t >= 200:
+                ts.append(t)
+                amps.append(2 / n * np.sum(uu[0, :, 0, 0] * np.sin(k * z)))
+            L.step(100)
+        slope = np.polyfit(np.array(ts), np.log(np.array(amps)), 1)[0]
+        assert abs(-slope / (k * k) / nu - 1) < 1e-3
+
+
+def pin_trt_poiseuille_magic(lib=None):
+    """With Lambda = 3/16 halfway bounce-back is exact for the Poiseuille
+    flow at ANY tau: the steady profile is g/(2 nu)(y - 1/2)(ny - 3/2 - y)."""
+    ny, g = 18, 1e-6
+    fl = np.zeros((1, ny, 1), dtype=np.uint8)
+    fl[:, 0] = W.WALL
+    fl[:, -1] = W.WALL
+    for tau in (0.55, 0.8, 1.7):
+        nu = (tau - 0.5) / 3
+        L = O.Lattice(1, ny, 1, tau, flags=fl, force=(g, 0, 0), lib=lib,
+                      omega_minus=O.trt_omega_minus(tau, 3.0 / 16.0))
+        L.step(60000 if tau < 0.6 else 30000)
+        _, u = L.moments()
+        ux = u[0, 0, 1:-1, 0]
+        y = np.arange(1, ny - 1)
+        exact = g / (2 * nu) * (y - 0.5) * (ny - 1.5 - y)
+        assert np.abs(ux - exact).max() < 1e-9 * exact.max(), f"tau {tau}"
+
+
 ALL_PINS = [
     pin_lattice_tables,
     pin_equilibrium_moments,
@@ -393,4 +500,9 @@ ALL_PINS = [
     pin_poiseuille,
     pin_cavity_mirror,
     pin_brute_force,
+    pin_trt_reduces_to_bgk,
+    pin_trt_single_cell,
+    pin_trt_conservation,
+    pin_trt_viscosity,
+    pin_trt_poiseuille_magic,
 ]

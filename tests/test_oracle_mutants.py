@@ -30,6 +30,11 @@ MUTANTS = {
     "guo_cc_coeff": ("9.0 * cu * lbo_c[i][a]", "3.0 * cu * lbo_c[i][a]"),
     "no_half_force": ("u[a] = j[a] / r + 0.5 * g[a];", "u[a] = j[a] / r;"),
     "omega_is_tau": ("double omega = 1.0 / tau;", "double omega = 2.0 - 1.0 / tau;"),
+    "trt_odd_rate_is_even": ("- wm * (fm - em)", "- wp * (fm - em)"),
+    "trt_even_rate_is_odd": ("- wp * (fp - ep)", "- wm * (fp - ep)"),
+    "trt_guo_odd_scale": ("(1.0 - 0.5 * wm) * gm", "(1.0 - 0.5 * wp) * gm"),
+    "trt_guo_even_scale": ("(1.0 - 0.5 * wp) * gp", "(1.0 - 0.5 * wm) * gp"),
+    "trt_odd_part_sign": ("fm = 0.5 * (f[i] - f[o])", "fm = 0.5 * (f[o] - f[i])"),
     "layout_transposed": ("(size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * (size_t)z)",
                           "(size_t)y + (size_t)ny * ((size_t)x + (size_t)nx * (size_t)z)"),
 }
