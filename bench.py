@@ -56,6 +56,12 @@ def parse_args(argv=None):
     ap.add_argument("--n", type=int, default=256, help="lattice edge (default 256)")
     ap.add_argument("--kernel", type=int, default=0, help="step kernel variant (0 = library choice)")
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--inplace", action="store_true",
+                    help="one population array updated in place (AA pattern) instead of two")
+    ap.add_argument("--trt-magic", type=float, default=0.0,
+                    help="two-relaxation-time collision with this magic parameter (0 = BGK)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the short runs of the other storage / layout forms in the default line")
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -252,7 +258,7 @@ def run_ours(args, dist: Dist):
     stream = torch.cuda.current_stream(dev)
     rho0, u0 = tgv_inputs(n)
     lat = Lattice(n, n, n, tau, storage=args.storage, device=dev, stream=stream,
-                  kernel=args.kernel, block=args.block)
+                  kernel=args.kernel, block=args.block, inplace=args.inplace, trt_magic=args.trt_magic)
     lat.init_fields(rho0, u0)
     tuned = None
     if args.kernel == 0 and not args.no_autotune:
@@ -319,7 +325,8 @@ def run_ours(args, dist: Dist):
     achieved = bpu * N / (kernel_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
-            "traffic": ncu_traffic(f"step_{args.storage}_tgv{n}", tuned[0] if tuned else args.kernel),
+            "traffic": ncu_traffic(f"step_{args.storage}_tgv{n}" + ("_inplace" if args.inplace else ""),
+                                   tuned[0] if tuned else args.kernel),
             "algorithmic_bytes_per_launch": bpu * N, "kernel": "lb step kernel",
             "kernel_ms_mean": round(kernel_ms, 5), "kernel_ms_median": round(statistics.median(step_ms), 5)}
 
@@ -332,6 +339,8 @@ def run_ours(args, dist: Dist):
         "config": {"workload": f"taylor-green vortex {n}^3, D3Q19 BGK, {args.storage} populations "
                                f"(f - w), tau={tau}, u0=0.05, k=2pi/{n}",
                    "lattice": [n, n, n], "storage": args.storage, "tau": tau,
+                   "populations": "one array, in place (AA pattern)" if args.inplace else "two arrays (A -> B)",
+                   "collision": f"TRT, magic {args.trt_magic}" if args.trt_magic else "BGK",
                    "check_every": args.check_every,
                    "kernel": ({"variant": tuned[0], "block": tuned[1], "chosen_by": "lb_autotune"}
                               if tuned else {"variant": args.kernel, "block": args.block,
@@ -347,6 +356,47 @@ def run_ours(args, dist: Dist):
     }
     lat.close()
     return line
+
+
+# ---------------------------------------------------------------- other forms
+def forms_section(n, steps=200, device=None):
+    """Short timed runs of the same Taylor-Green lattice in the other storage
+    forms, the in-place layout and the TRT collision (autotuned kernel, CUDA
+    events on the lattice's stream, 5 warm-up steps): GLUPS and the fraction
+    of the measured HBM bandwidth at the algorithmic bytes per update."""
+    import torch
+
+    from paper_2409_16781_gb300 import Lattice
+    peak, peak_kind = measured_peaks()
+    rho0, u0 = tgv_inputs(n)
+    out = []
+    for storage, inplace, trt in (("f16s", False, 0.0), ("bf16s", False, 0.0), ("f64", False, 0.0),
+                                  ("f32d", False, 0.0), ("f32", False, 3 / 16), ("f32", True, 0.0),
+                                  ("f16s", True, 0.0)):
+        stream = torch.cuda.current_stream(device)
+        lat = Lattice(n, n, n, 0.55, storage=storage, stream=stream, device=device, inplace=inplace,
+                      trt_magic=trt)
+        lat.init_fields(rho0, u0)
+        v, b, _ = lat.autotune(reps=10, cache=False)
+        k = steps if STORAGE_BYTES[storage] <= 4 and storage != "f32d" else steps // 4
+        lat.step(5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(device)
+        e0.record(stream)
+        lat.step(k)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        glups = n ** 3 / ms / 1e6
+        gbs = glups * bytes_per_update(storage)
+        out.append({"storage": storage, "populations": "in place" if inplace else "two arrays",
+                    "collision": "TRT 3/16" if trt else "BGK", "variant": v, "block": b, "steps": k,
+                    "glups": round(glups, 2), "gbs": round(gbs, 1),
+                    "frac": round(gbs / peak, 4), "peak_kind": peak_kind,
+                    "bytes_per_update": bytes_per_update(storage)})
+        lat.close()
+        del lat
+    return out
 
 
 # ---------------------------------------------------------------- serving
@@ -501,6 +551,8 @@ def main(argv=None):
                 print(json.dumps(fn(args)), flush=True)
             return 0
         line = run_ours(args, dist)
+        if dist.rank == 0 and dist.world == 1 and not args.no_forms:
+            line["other_forms"] = forms_section(args.n)
         if dist.rank == 0 and dist.world == 1 and args.serve_requests > 0:
             line["serving"] = run_serving(args.serve_requests, (2.0,), args.serve_budget_gb)
         elif dist.rank == 0:

@@ -75,7 +75,26 @@ typedef struct lb_options {
     double force[3];   /* body force per unit mass g (Guo forcing, the S_i
                           of Eq. 1); default 0 */
     void *stream;      /* cudaStream_t to issue work on; NULL = default */
-    int reserved[8];
+    double trt_magic;  /* collision: 0 = BGK (Eq. 1, one rate omega = 1/tau,
+                          the default); > 0 = two-relaxation-time collision
+                          (Ginzburg's TRT, not in the paper): the part of f
+                          even under c -> -c relaxes at 1/tau, the odd part
+                          at omega_m with (tau - 1/2)(1/omega_m - 1/2) =
+                          trt_magic, and the Guo source splits the same way.
+                          3/16 makes halfway bounce-back walls exact for
+                          Poiseuille flow at any tau.  Must be >= 0. */
+    int inplace;       /* 0 (default): two population arrays, the paper's
+                          fused scheme (Sec. 3.1: read f^pre, write f^post,
+                          swap).  1: ONE array, updated in place with the
+                          "AA" access pattern (not in the paper): the steps
+                          alternate between two layouts of the same array,
+                          each thread writing exactly the values it read, so
+                          the lattice needs half the population memory for
+                          the same bytes per update.  lb_step then ignores
+                          the variant (one cell per thread); values that
+                          lb_get_populations reports for solid cells are
+                          the rest state f = w. */
+    int reserved[5];
 } lb_options;
 
 /* Fill *opt with the defaults (FP32, no force, default stream). */
@@ -152,17 +171,23 @@ int lb_get_populations_at(lb_lattice *h, const int64_t *cells, int n, double *ou
  * (16-bit storage, even nx); 8, 9 four cells per thread, packed 16-bit
  * (16-bit storage, nx % 4 == 0); 10, 11, 12 TMA bulk-copy pipeline
  * through shared memory, four / two / one cells per thread (16-bit storage,
- * nx % 16 == 0; block size fixed).  A variant that
- * does not apply to the
- * lattice runs variant 1.  block = threads per block (0 = default; rounded
- * down to whole warps). */
+ * nx % 16 == 0; block size fixed); 13 two cells per thread collided together
+ * in packed FP32 (f32x2) arithmetic (FP32 or 16-bit storage, even nx); 14
+ * four cells per thread, collided as two packed pairs (16-bit storage,
+ * nx % 4 == 0).  A variant that does not apply to the lattice runs
+ * variant 1.  block = threads per block (0 = default; rounded down to whole
+ * warps). */
 int lb_set_kernel(lb_lattice *h, int variant, int block);
 
 /* Autotuner: time every applicable (variant, block) pair on this lattice
  * with `reps` launches each (CUDA events on the lattice's stream), keep the
  * fastest for later lb_step calls and report it (outputs may be NULL).
  * The timed launches read array A and write array B only, so the lattice
- * state is unchanged.  Synchronises the stream. */
+ * state is unchanged.  An in-place lattice has no second array: its
+ * populations are copied to host memory (malloc'd here, 19*N*sizeof(pop)
+ * bytes) before the timed steps and copied back after them, so its state is
+ * unchanged too (LB_ENOMEM if the host buffer cannot be had).  Synchronises
+ * the stream. */
 int lb_autotune(lb_lattice *h, int reps, int *variant, int *block, float *ms_per_step);
 
 /* Totals without any allocation (the paper has no counterpart: it is a

@@ -26,7 +26,9 @@ class LbOptions(ctypes.Structure):
         ("reserved0", ctypes.c_int),
         ("force", ctypes.c_double * 3),
         ("stream", ctypes.c_void_p),
-        ("reserved", ctypes.c_int * 8),
+        ("trt_magic", ctypes.c_double),
+        ("inplace", ctypes.c_int),
+        ("reserved", ctypes.c_int * 5),
     ]
 
 

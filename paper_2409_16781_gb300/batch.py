@@ -80,10 +80,11 @@ class Batch:
 
     # ------------------------------------------------------------------
     def add(self, nx, ny, nz, tau, steps, u_lid=(0.0, 0.0, 0.0), flags=None, storage="f32",
-            force=(0.0, 0.0, 0.0)) -> int:
+            force=(0.0, 0.0, 0.0), trt_magic=0.0) -> int:
         """Admit a lattice; returns its slot.  Raises LbError with status
-        LB_ENOMEM (pool full) or LB_EBUSY (no free slot) when it does not fit."""
-        opts = make_options(storage, force)
+        LB_ENOMEM (pool full) or LB_EBUSY (no free slot) when it does not fit.
+        trt_magic > 0 selects the two-relaxation-time collision."""
+        opts = make_options(storage, force, trt_magic=trt_magic)
         ulid = (ctypes.c_double * 3)(*[float(v) for v in u_lid])
         fl = None
         if flags is not None:

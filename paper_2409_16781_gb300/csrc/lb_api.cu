@@ -10,6 +10,7 @@
 
 #include "lbgb.h"
 #include "lb_internal.h"
+#include "lb_kernels.cuh"
 
 using namespace lbgb;
 
@@ -17,12 +18,15 @@ struct lb_lattice {
     int nx, ny, nz;
     int64_t N, ps;
     int storage, sbytes;
-    double tau, ulid[3], g[3];
+    double tau, omega_m, ulid[3], g[3];
     void* base;
     bool owns;
     size_t bytes;
-    void* pop[2];  // pop[cur] holds the current post-collision array A
+    void* pop[2];  // pop[cur] holds the current post-collision array A (in
+                   // place: pop[0] == pop[1], the one array)
     int cur;
+    int inplace;   // one population array, AA access pattern
+    int form;      // layout of the state: FORM_AB, or FORM_SWAPPED / FORM_STREAMED in place
     uint8_t* code;
     double* partials;
     double* tot_out;
@@ -67,12 +71,12 @@ bool valid_dims(int nx, int ny, int nz) {
     return N < (int64_t(1) << 31);
 }
 
-Layout layout_for(int nx, int ny, int nz, int storage) {
+Layout layout_for(int nx, int ny, int nz, int storage, int inplace) {
     Layout L{};
     L.N = (int64_t)nx * ny * nz;
     L.ps = (int64_t)round_up((size_t)L.N, 128);
     L.pop_bytes = round_up((size_t)Q * L.ps * storage_bytes(storage), ALIGN);
-    size_t off = 2 * L.pop_bytes;
+    size_t off = (inplace ? 1 : 2) * L.pop_bytes;
     L.code_off = off;
     off += round_up((size_t)L.N, ALIGN);
     L.part_off = off;
@@ -106,6 +110,7 @@ LatticeParams params_of(const lb_lattice* h) {
     p.N = h->N;
     p.ps = h->ps;
     p.omega = 1.0 / h->tau;
+    p.omega_m = h->omega_m;
     for (int a = 0; a < 3; ++a) {
         p.g[a] = h->g[a];
         p.ulid[a] = h->ulid[a];
@@ -142,11 +147,14 @@ int create_common(lb_lattice** out, int nx, int ny, int nz, double tau, const do
     if (!valid_dims(nx, ny, nz)) return fail(LB_EINVAL, "lb_create: bad dims %d x %d x %d", nx, ny, nz);
     if (!(tau > 0.5) || !std::isfinite(tau)) return fail(LB_EINVAL, "lb_create: tau must be > 1/2 (got %g)", tau);
     if (o.storage < LB_F64 || o.storage > LB_F32D) return fail(LB_EINVAL, "lb_create: bad storage %d", o.storage);
+    if (!(o.trt_magic >= 0.0) || !std::isfinite(o.trt_magic))
+        return fail(LB_EINVAL, "lb_create: trt_magic must be >= 0 (got %g)", o.trt_magic);
+    if (o.inplace != 0 && o.inplace != 1) return fail(LB_EINVAL, "lb_create: inplace must be 0 or 1 (got %d)", o.inplace);
     for (int a = 0; a < 3; ++a) {
         if (!std::isfinite(o.force[a])) return fail(LB_EINVAL, "lb_create: non-finite force");
         if (u_lid && !std::isfinite(u_lid[a])) return fail(LB_EINVAL, "lb_create: non-finite u_lid");
     }
-    const Layout L = layout_for(nx, ny, nz, o.storage);
+    const Layout L = layout_for(nx, ny, nz, o.storage, o.inplace);
     if (flags) {
         for (int64_t c = 0; c < L.N; ++c)
             if (flags[c] > LB_LID) return fail(LB_EINVAL, "lb_create: flag %d at cell %lld", flags[c], (long long)c);
@@ -165,6 +173,7 @@ int create_common(lb_lattice** out, int nx, int ny, int nz, double tau, const do
     h->storage = o.storage;
     h->sbytes = storage_bytes(o.storage);
     h->tau = tau;
+    h->omega_m = trt_omega_minus(tau, o.trt_magic);
     for (int a = 0; a < 3; ++a) {
         h->ulid[a] = u_lid ? u_lid[a] : 0.0;
         h->g[a] = o.force[a];
@@ -186,8 +195,10 @@ int create_common(lb_lattice** out, int nx, int ny, int nz, double tau, const do
         h->owns = true;
     }
     char* b = (char*)h->base;
+    h->inplace = o.inplace;
+    h->form = o.inplace ? FORM_SWAPPED : FORM_AB;
     h->pop[0] = b;
-    h->pop[1] = b + L.pop_bytes;
+    h->pop[1] = o.inplace ? b : b + L.pop_bytes;
     h->cur = 0;
     h->code = (uint8_t*)(b + L.code_off);
     h->partials = (double*)(b + L.part_off);
@@ -212,7 +223,8 @@ int create_common(lb_lattice** out, int nx, int ny, int nz, double tau, const do
     if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
     if (e != cudaSuccess) rc = cuda_fail(e, "lb_create: flags");
     if (rc == LB_OK) {
-        e = launch_init(h->storage, h->pop[0], h->pop[1], h->ps, nullptr, nullptr, 0, 0, h->N, h->stream);
+        e = launch_init(h->storage, h->pop[0], h->pop[1], h->ps, nullptr, nullptr, 0, 0, h->N, h->stream,
+                        h->inplace);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) rc = cuda_fail(e, "lb_create: init");
     }
@@ -247,8 +259,9 @@ int lb_velocity_set(int* c, double* w) {
 
 size_t lb_bytes_required(int nx, int ny, int nz, const lb_options* opt) {
     const int storage = opt ? opt->storage : LB_F32;
-    if (!valid_dims(nx, ny, nz) || storage < LB_F64 || storage > LB_F32D) return 0;
-    return layout_for(nx, ny, nz, storage).total;
+    const int inplace = opt ? opt->inplace : 0;
+    if (!valid_dims(nx, ny, nz) || storage < LB_F64 || storage > LB_F32D || (inplace != 0 && inplace != 1)) return 0;
+    return layout_for(nx, ny, nz, storage, inplace).total;
 }
 
 int lb_create(lb_lattice** out, int nx, int ny, int nz, double tau, const double* u_lid, const uint8_t* flags,
@@ -266,8 +279,10 @@ int lb_init_fields(lb_lattice* h, const double* rho, const double* u) {
     if (!h) return fail(LB_EINVAL, "lb_init_fields: NULL handle");
     const size_t per_cell = (rho ? 8 : 0) + (u ? 24 : 0);
     if (per_cell == 0) {
-        cudaError_t e = launch_init(h->storage, h->pop[0], h->pop[1], h->ps, nullptr, nullptr, 0, 0, h->N, h->stream);
+        cudaError_t e = launch_init(h->storage, h->pop[0], h->pop[1], h->ps, nullptr, nullptr, 0, 0, h->N, h->stream,
+                                    h->inplace);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (h->inplace) h->form = FORM_SWAPPED;
         return e == cudaSuccess ? LB_OK : cuda_fail(e, "lb_init_fields");
     }
     const int64_t chunk = chunk_cells(h, per_cell);
@@ -281,8 +296,10 @@ int lb_init_fields(lb_lattice* h, const double* rho, const double* u) {
         for (int a = 0; a < 3 && u && e == cudaSuccess; ++a)
             e = cudaMemcpyAsync(du + a * cnt, u + a * h->N + c0, cnt * 8, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess)
-            e = launch_init(h->storage, h->pop[h->cur], h->pop[1 - h->cur], h->ps, drho, du, cnt, c0, cnt, h->stream);
+            e = launch_init(h->storage, h->pop[h->cur], h->pop[1 - h->cur], h->ps, drho, du, cnt, c0, cnt, h->stream,
+                            h->inplace);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (h->inplace) h->form = FORM_SWAPPED;  // cells already written are in that layout
         if (e != cudaSuccess) return cuda_fail(e, "lb_init_fields");
     }
     return LB_OK;
@@ -293,10 +310,17 @@ int lb_step(lb_lattice* h, int n) {
     if (n < 0) return fail(LB_EINVAL, "lb_step: n < 0");
     const LatticeParams p = params_of(h);
     for (int t = 0; t < n; ++t) {
-        cudaError_t e = launch_step(h->storage, h->kernel, h->pop[h->cur], h->pop[1 - h->cur], h->code, p, h->block,
-                                    h->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "lb_step");
-        h->cur = 1 - h->cur;
+        if (h->inplace) {
+            cudaError_t e = launch_step_inplace(h->storage, h->kernel, h->pop[0], h->code, p, h->form, h->block,
+                                                h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "lb_step");
+            h->form = h->form == FORM_SWAPPED ? FORM_STREAMED : FORM_SWAPPED;
+        } else {
+            cudaError_t e = launch_step(h->storage, h->kernel, h->pop[h->cur], h->pop[1 - h->cur], h->code, p,
+                                        h->block, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "lb_step");
+            h->cur = 1 - h->cur;
+        }
         h->steps++;
     }
     return LB_OK;
@@ -305,7 +329,7 @@ int lb_step(lb_lattice* h, int n) {
 int lb_moments_device(lb_lattice* h, double* rho_dev, double* u_dev) {
     if (!h) return fail(LB_EINVAL, "lb_moments_device: NULL handle");
     cudaError_t e = launch_moments(h->storage, h->pop[h->cur], h->code, params_of(h), rho_dev, u_dev, h->N, 0, h->N,
-                                   h->stream);
+                                   h->stream, h->form);
     return e == cudaSuccess ? LB_OK : cuda_fail(e, "lb_moments_device");
 }
 
@@ -317,7 +341,8 @@ int lb_moments(lb_lattice* h, double* rho, double* u) {
     const LatticeParams p = params_of(h);
     for (int64_t c0 = 0; c0 < h->N; c0 += chunk) {
         const int64_t cnt = (h->N - c0 < chunk) ? h->N - c0 : chunk;
-        cudaError_t e = launch_moments(h->storage, h->pop[h->cur], h->code, p, st, st + cnt, cnt, c0, cnt, h->stream);
+        cudaError_t e =
+            launch_moments(h->storage, h->pop[h->cur], h->code, p, st, st + cnt, cnt, c0, cnt, h->stream, h->form);
         if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho + c0, st, cnt * 8, cudaMemcpyDeviceToHost, h->stream);
         for (int a = 0; a < 3 && u && e == cudaSuccess; ++a)
             e = cudaMemcpyAsync(u + a * h->N + c0, st + (1 + a) * cnt, cnt * 8, cudaMemcpyDeviceToHost, h->stream);
@@ -331,7 +356,7 @@ int lb_totals(lb_lattice* h, double* mass, double* mom) {
     if (!h) return fail(LB_EINVAL, "lb_totals: NULL handle");
     double out[5];
     cudaError_t e = launch_totals(h->storage, h->pop[h->cur], h->code, params_of(h), h->partials, h->tot_out,
-                                  h->stream);
+                                  h->stream, h->form);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, h->tot_out, sizeof out, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "lb_totals");
@@ -351,7 +376,8 @@ int lb_get_populations(lb_lattice* h, double* f) {
     double* st = (double*)h->staging;
     for (int64_t c0 = 0; c0 < h->N; c0 += chunk) {
         const int64_t cnt = (h->N - c0 < chunk) ? h->N - c0 : chunk;
-        cudaError_t e = launch_get_pops(h->storage, h->pop[h->cur], h->ps, c0, cnt, st, h->stream);
+        cudaError_t e = launch_get_pops(h->storage, h->pop[h->cur], h->code, params_of(h), h->form, c0, cnt, st,
+                                        h->stream);
         for (int i = 0; i < Q && e == cudaSuccess; ++i)
             e = cudaMemcpyAsync(f + i * h->N + c0, st + i * cnt, cnt * 8, cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -370,8 +396,10 @@ int lb_set_populations(lb_lattice* h, const double* f) {
         for (int i = 0; i < Q && e == cudaSuccess; ++i)
             e = cudaMemcpyAsync(st + i * cnt, f + i * h->N + c0, cnt * 8, cudaMemcpyHostToDevice, h->stream);
         if (e == cudaSuccess)
-            e = launch_set_pops(h->storage, h->pop[h->cur], h->pop[1 - h->cur], h->ps, c0, cnt, st, h->stream);
+            e = launch_set_pops(h->storage, h->pop[h->cur], h->pop[1 - h->cur], h->ps, c0, cnt, st, h->stream,
+                                h->inplace);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (h->inplace) h->form = FORM_SWAPPED;  // cells already written are in that layout
         if (e != cudaSuccess) return cuda_fail(e, "lb_set_populations");
     }
     return LB_OK;
@@ -392,7 +420,9 @@ int lb_get_populations_at(lb_lattice* h, const int64_t* cells, int n, double* ou
         int64_t* dcells = (int64_t*)st;
         double* dout = (double*)(st + round_up((size_t)cnt * 8, ALIGN));
         cudaError_t e = cudaMemcpyAsync(dcells, cells + k0, (size_t)cnt * 8, cudaMemcpyHostToDevice, h->stream);
-        if (e == cudaSuccess) e = launch_gather_pops(h->storage, h->pop[h->cur], h->ps, dcells, cnt, dout, h->stream);
+        if (e == cudaSuccess)
+            e = launch_gather_pops(h->storage, h->pop[h->cur], h->code, params_of(h), h->form, dcells, cnt, dout,
+                                   h->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(out + k0 * Q, dout, (size_t)cnt * Q * 8, cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -403,10 +433,63 @@ int lb_get_populations_at(lb_lattice* h, const int64_t* cells, int n, double* ou
 
 int lb_set_kernel(lb_lattice* h, int variant, int block) {
     if (!h) return fail(LB_EINVAL, "lb_set_kernel: NULL handle");
-    if (variant < 0 || variant > 12 || block < 0 || block > 1024)
+    if (variant < 0 || variant > 14 || block < 0 || block > 1024)
         return fail(LB_EINVAL, "lb_set_kernel: bad variant %d / block %d", variant, block);
     h->kernel = variant;
     h->block = block;
+    return LB_OK;
+}
+
+// Autotuning an in-place lattice: its steps rewrite the one array, so the
+// populations are copied to host memory first and copied back (with the
+// layout) after the timed steps.
+static int autotune_inplace(lb_lattice* h, int reps, int* variant, int* block, float* ms_per_step) {
+    const size_t bytes = (size_t)Q * h->ps * h->sbytes;
+    char* snap = new (std::nothrow) char[bytes];
+    if (!snap) return fail(LB_ENOMEM, "lb_autotune: no host memory for the %zu-byte snapshot", bytes);
+    const int form0 = h->form;
+    cudaError_t e = cudaMemcpyAsync(snap, h->pop[0], bytes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const LatticeParams p = params_of(h);
+    const int blocks[] = {32, 64, 128, 256, 512};
+    int best = -1;
+    float best_ms = 0.f;
+    int form = h->form;
+    auto one = [&](int b) {
+        cudaError_t r = launch_step_inplace(h->storage, 1, h->pop[0], h->code, p, form, b, h->stream);
+        form = form == FORM_SWAPPED ? FORM_STREAMED : FORM_SWAPPED;
+        return r;
+    };
+    for (int c = 0; c < 5 && e == cudaSuccess; ++c) {
+        e = one(blocks[c]);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = one(blocks[c]);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && (best < 0 || ms < best_ms)) {
+            best = c;
+            best_ms = ms;
+        }
+    }
+    // restore the state whatever happened above
+    cudaError_t er = cudaMemcpyAsync(h->pop[0], snap, bytes, cudaMemcpyHostToDevice, h->stream);
+    if (er == cudaSuccess) er = cudaStreamSynchronize(h->stream);
+    h->form = form0;
+    delete[] snap;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "lb_autotune");
+    if (er != cudaSuccess) return cuda_fail(er, "lb_autotune: restore");
+    h->kernel = 1;
+    h->block = blocks[best];
+    if (variant) *variant = h->kernel;
+    if (block) *block = h->block;
+    if (ms_per_step) *ms_per_step = best_ms / reps;
     return LB_OK;
 }
 
@@ -422,12 +505,17 @@ int lb_autotune(lb_lattice* h, int reps, int* variant, int* block, float* ms_per
         if (nc < 32) cands[nc++] = {v, b};
     };
     const bool sixteen = h->sbytes == 2;
+    if (h->inplace) return autotune_inplace(h, reps, variant, block, ms_per_step);
     for (int b : {32, 64, 128, 256}) add(1, b);
     if (h->nx % 2 == 0) {
         for (int b : {64, 128}) add(sixteen ? 6 : 4, b);
     }
     if (sixteen && h->nx % 4 == 0) {
         for (int b : {32, 64, 128}) add(8, b);
+        for (int b : {32, 64, 128}) add(14, b);
+    }
+    if ((sixteen || h->storage == LB_F32) && h->nx % 2 == 0) {
+        for (int b : {32, 64, 128}) add(13, b);
     }
     if (sixteen && h->nx % 16 == 0) {
         add(10, 0);

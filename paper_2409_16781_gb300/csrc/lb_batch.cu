@@ -685,6 +685,8 @@ int lb_batch_add(lb_batch* b, int nx, int ny, int nz, double tau, const double* 
         return bfail(LB_EINVAL, "lb_batch_add: bad dims %d x %d x %d", nx, ny, nz);
     if (!(tau > 0.5) || !std::isfinite(tau)) return bfail(LB_EINVAL, "lb_batch_add: tau must be > 1/2");
     if (o.storage < LB_F64 || o.storage > LB_F32D) return bfail(LB_EINVAL, "lb_batch_add: bad storage");
+    if (!(o.trt_magic >= 0.0) || !std::isfinite(o.trt_magic))
+        return bfail(LB_EINVAL, "lb_batch_add: trt_magic must be >= 0");
     if (steps < 0) return bfail(LB_EINVAL, "lb_batch_add: steps < 0");
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(o.force[a]) || (u_lid && !std::isfinite(u_lid[a])))
@@ -718,6 +720,7 @@ int lb_batch_add(lb_batch* b, int nx, int ny, int nz, double tau, const double* 
     d.p.N = N;
     d.p.ps = ps;
     d.p.omega = 1.0 / tau;
+    d.p.omega_m = trt_omega_minus(tau, o.trt_magic);
     for (int a = 0; a < 3; ++a) {
         d.p.g[a] = o.force[a];
         d.p.ulid[a] = u_lid ? u_lid[a] : 0.0;
@@ -995,7 +998,7 @@ int lb_batch_get_populations(lb_batch* b, int slot, double* f) {
     const int64_t chunk = bchunk(b, Q * 8);
     for (int64_t c0 = 0; c0 < N; c0 += chunk) {
         const int64_t cnt = (N - c0 < chunk) ? N - c0 : chunk;
-        cudaError_t e = launch_get_pops(d.storage, d.pop[par], d.p.ps, c0, cnt, stg, st);
+        cudaError_t e = launch_get_pops(d.storage, d.pop[par], d.code, d.p, FORM_AB, c0, cnt, stg, st);
         for (int i = 0; i < Q && e == cudaSuccess; ++i)
             e = cudaMemcpyAsync(f + i * N + c0, stg + i * cnt, cnt * 8, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -99,7 +99,8 @@ struct LatticeParams {
     int nx, ny, nz;
     int64_t N;        // nx*ny*nz
     int64_t ps;       // plane stride between populations (elements), >= N
-    double omega;     // 1/tau
+    double omega;     // 1/tau: rate of the part of f even under c -> -c
+    double omega_m;   // rate of the odd part (two-relaxation-time); = omega for BGK
     double g[3];      // body force per unit mass
     double ulid[3];   // lid velocity
     int* err;         // device error word (bounded waits that gave up), or nullptr

@@ -13,18 +13,24 @@ cudaError_t launch_classify(const uint8_t* flags, uint8_t* code, int nx, int ny,
 cudaError_t launch_step(int storage, int variant, const void* A, void* B, const uint8_t* code,
                         const LatticeParams& p, int block, cudaStream_t st);
 cudaError_t launch_init(int storage, void* A, void* B, int64_t ps, const double* rho, const double* u,
-                        int64_t ustride, int64_t c0, int64_t count, cudaStream_t st);
+                        int64_t ustride, int64_t c0, int64_t count, cudaStream_t st, int swapped = 0);
+// `form` (FORM_AB, FORM_SWAPPED, FORM_STREAMED of lb_kernels.cuh): where
+// the state keeps its post-collision values.
 cudaError_t launch_moments(int storage, const void* A, const uint8_t* code, const LatticeParams& p, double* rho,
-                           double* u, int64_t ustride, int64_t c0, int64_t count, cudaStream_t st);
+                           double* u, int64_t ustride, int64_t c0, int64_t count, cudaStream_t st, int form = 0);
 int totals_blocks(int64_t N);
 cudaError_t launch_totals(int storage, const void* A, const uint8_t* code, const LatticeParams& p,
-                          double* partials, double* out5, cudaStream_t st);
-cudaError_t launch_get_pops(int storage, const void* A, int64_t ps, int64_t c0, int64_t count, double* buf,
-                            cudaStream_t st);
+                          double* partials, double* out5, cudaStream_t st, int form = 0);
+cudaError_t launch_get_pops(int storage, const void* A, const uint8_t* code, const LatticeParams& p, int form,
+                            int64_t c0, int64_t count, double* buf, cudaStream_t st);
 cudaError_t launch_set_pops(int storage, void* A, void* B, int64_t ps, int64_t c0, int64_t count,
-                            const double* buf, cudaStream_t st);
-cudaError_t launch_gather_pops(int storage, const void* A, int64_t ps, const int64_t* cells, int n, double* out,
-                               cudaStream_t st);
+                            const double* buf, cudaStream_t st, int swapped = 0);
+cudaError_t launch_gather_pops(int storage, const void* A, const uint8_t* code, const LatticeParams& p, int form,
+                               const int64_t* cells, int n, double* out, cudaStream_t st);
+// In-place (AA) step: from the state in layout `form` (FORM_SWAPPED or
+// FORM_STREAMED) to the other layout, one array.
+cudaError_t launch_step_inplace(int storage, int variant, void* A, const uint8_t* code, const LatticeParams& p,
+                                int form, int block, cudaStream_t st);
 
 // Instantiate CALL with S = the storage type of `storage` and return it.
 #define LBGB_DISPATCH(storage, CALL)                      \
@@ -36,6 +42,17 @@ cudaError_t launch_gather_pops(int storage, const void* A, int64_t ps, const int
         case 4: { using S = f32d; return CALL; }          \
         default: return cudaErrorInvalidValue;            \
     }
+
+// Rate of the odd part of the populations.  magic = 0: BGK (omega_m =
+// 1/tau).  magic > 0: two-relaxation-time collision with the parameter
+// Lambda = (tau - 1/2)(1/omega_m - 1/2) = magic held fixed, so that wall
+// positions and the steady solution depend on Lambda only (Ginzburg's
+// TRT; Lambda = 3/16 puts halfway bounce-back walls exactly halfway for the
+// Poiseuille profile).
+inline double trt_omega_minus(double tau, double magic) {
+    if (magic == 0.0) return 1.0 / tau;
+    return 1.0 / (magic / (tau - 0.5) + 0.5);
+}
 
 inline int storage_bytes(int storage) {
     switch (storage) {

@@ -42,11 +42,14 @@ __global__ void classify_kernel(const uint8_t* __restrict__ flags, uint8_t* __re
 // ---------------------------------------------------------------------------
 // Equilibrium initialisation of cells [c0, c0+count): d_i = f^eq_i - w_i.
 // rho/u are chunk-local (index cell - c0; u SoA with stride ustride), NULL =
-// rho 1 / u 0.  Both arrays are written.
+// rho 1 / u 0.  Both arrays are written (the same array for the in-place
+// scheme, whose state then has the swapped layout: direction i in plane
+// opp(i)).
 // ---------------------------------------------------------------------------
 template <class S>
-__global__ void init_kernel(S* __restrict__ A, S* __restrict__ B, int64_t ps, const double* __restrict__ rho,
-                            const double* __restrict__ u, int64_t ustride, int64_t c0, int64_t count) {
+__global__ void init_kernel(S* A, S* B, int64_t ps, const double* __restrict__ rho,
+                            const double* __restrict__ u, int64_t ustride, int64_t c0, int64_t count,
+                            int swapped) {
     using M = typename Storage<S>::math;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count;
          k += (int64_t)gridDim.x * blockDim.x) {
@@ -62,8 +65,9 @@ __global__ void init_kernel(S* __restrict__ A, S* __restrict__ B, int64_t ps, co
             const M cu = D3Q19::cx(i) * ux + D3Q19::cy(i) * uy + D3Q19::cz(i) * uz;
             const M dv = (M)D3Q19::w(i) * (drho + r * (M(3) * cu + M(4.5) * cu * cu - uu15));
             const S s = Storage<S>::store(dv);
-            A[i * ps + cell] = s;
-            B[i * ps + cell] = s;
+            const int plane = swapped ? D3Q19::opp(i) : i;
+            A[plane * ps + cell] = s;
+            B[plane * ps + cell] = s;
         }
     }
 }
@@ -72,7 +76,7 @@ __global__ void init_kernel(S* __restrict__ A, S* __restrict__ B, int64_t ps, co
 // Moments of cells [c0, c0+count) into chunk-local rho (count) and u (SoA,
 // stride ustride).  Solid cells: 0.
 // ---------------------------------------------------------------------------
-template <class S>
+template <class S, int FORM>
 __global__ void moments_kernel(const S* __restrict__ A, const uint8_t* __restrict__ code, LatticeParams p,
                                double* __restrict__ rho, double* __restrict__ u, int64_t ustride, int64_t c0,
                                int64_t count) {
@@ -85,7 +89,7 @@ __global__ void moments_kernel(const S* __restrict__ A, const uint8_t* __restric
         if (!(cc & CODE_TYPE)) {
             const int x = cell % p.nx, y = (cell / p.nx) % p.ny, z = cell / (p.nx * p.ny);
             M d[Q];
-            pull_cell<S>(A, code, p, x, y, z, cell, cc, d);
+            pull_cell<S, 0, FORM>(A, code, p, x, y, z, cell, cc, d);
             M drho, mr, ux, uy, uz;
             macro_dev<M>(d, p, drho, mr, ux, uy, uz);
             r = mr;
@@ -116,7 +120,7 @@ constexpr int TOT_THREADS = 256;
 constexpr int TOT_FOLD = 8;
 constexpr int TOT_PARTS = 6;
 
-template <class S>
+template <class S, int FORM>
 __global__ void __launch_bounds__(TOT_THREADS) totals_kernel(const S* __restrict__ A,
                                                              const uint8_t* __restrict__ code,
                                                              LatticeParams p, double* __restrict__ partials) {
@@ -135,7 +139,7 @@ __global__ void __launch_bounds__(TOT_THREADS) totals_kernel(const S* __restrict
             const uint8_t cc = code[cell];
             if (!(cc & CODE_TYPE)) {
                 M d[Q];
-                pull_cell<S>(A, code, p, x, row % p.ny, row / p.ny, cell, cc, d);
+                pull_cell<S, 0, FORM>(A, code, p, x, row % p.ny, row / p.ny, cell, cc, d);
                 M drho, jx, jy, jz;
                 moment_sums<M>(d, drho, jx, jy, jz);
                 sd += drho;
@@ -202,22 +206,40 @@ __global__ void __launch_bounds__(TOT_THREADS) totals_finalize_kernel(const doub
 
 // ---------------------------------------------------------------------------
 // Population import / export (FP64 f = w + d), cells [c0, c0+count).
-// Chunk buffer layout: buf[i*count + k].
+// Chunk buffer layout: buf[i*count + k].  `form` is where the state keeps
+// P_i(x) (FORM_AB, FORM_SWAPPED, FORM_STREAMED); in the streamed layout a
+// solid cell has no values of its own and exports the rest state f = w.
 // ---------------------------------------------------------------------------
 template <class S>
-__global__ void get_pops_kernel(const S* __restrict__ A, int64_t ps, int64_t c0, int64_t count,
-                                double* __restrict__ buf) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count;
-         k += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-            buf[i * count + k] = D3Q19::w(i) + (double)Storage<S>::load(A[i * ps + c0 + k]);
-    }
+__device__ __forceinline__ double export_pop(const S* __restrict__ A, const uint8_t* __restrict__ code,
+                                             const LatticeParams& p, int form, int64_t cell, int i) {
+    if (form == FORM_AB) return D3Q19::w(i) + (double)Storage<S>::load(A[i * p.ps + cell]);
+    if (form == FORM_SWAPPED) return D3Q19::w(i) + (double)Storage<S>::load(A[D3Q19::opp(i) * p.ps + cell]);
+    if (code[cell] & CODE_TYPE) return D3Q19::w(i);
+    const int x = (int)(cell % p.nx), y = (int)((cell / p.nx) % p.ny), z = (int)(cell / ((int64_t)p.nx * p.ny));
+    int tx = x + D3Q19::cx_rt(i), ty = y + D3Q19::cy_rt(i), tz = z + D3Q19::cz_rt(i);
+    tx = tx < 0 ? tx + p.nx : (tx >= p.nx ? tx - p.nx : tx);
+    ty = ty < 0 ? ty + p.ny : (ty >= p.ny ? ty - p.ny : ty);
+    tz = tz < 0 ? tz + p.nz : (tz >= p.nz ? tz - p.nz : tz);
+    const int64_t t = tx + (int64_t)p.nx * (ty + (int64_t)p.ny * tz);
+    return D3Q19::w(i) + (double)Storage<S>::load(A[i * p.ps + t]);
 }
 
 template <class S>
-__global__ void set_pops_kernel(S* __restrict__ A, S* __restrict__ B, int64_t ps, int64_t c0, int64_t count,
-                                const double* __restrict__ buf) {
+__global__ void get_pops_kernel(const S* __restrict__ A, const uint8_t* __restrict__ code, LatticeParams p, int form,
+                                int64_t c0, int64_t count, double* __restrict__ buf) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count;
+         k += (int64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) buf[i * count + k] = export_pop<S>(A, code, p, form, c0 + k, i);
+    }
+}
+
+// Import: writes both arrays (two-array scheme) or, with `swapped`, the one
+// array of the in-place scheme in the swapped layout.
+template <class S>
+__global__ void set_pops_kernel(S* A, S* B, int64_t ps, int64_t c0, int64_t count,
+                                const double* __restrict__ buf, int swapped) {
     using M = typename Storage<S>::math;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count;
          k += (int64_t)gridDim.x * blockDim.x) {
@@ -225,20 +247,21 @@ __global__ void set_pops_kernel(S* __restrict__ A, S* __restrict__ B, int64_t ps
         for (int i = 0; i < Q; ++i) {
             const double dv = buf[i * count + k] - D3Q19::w(i);
             const S s = Storage<S>::store((M)dv);
-            A[i * ps + c0 + k] = s;
-            B[i * ps + c0 + k] = s;
+            const int plane = swapped ? D3Q19::opp(i) : i;
+            A[plane * ps + c0 + k] = s;
+            B[plane * ps + c0 + k] = s;
         }
     }
 }
 
 template <class S>
-__global__ void gather_pops_kernel(const S* __restrict__ A, int64_t ps, const int64_t* __restrict__ cells, int n,
-                                   double* __restrict__ out) {
+__global__ void gather_pops_kernel(const S* __restrict__ A, const uint8_t* __restrict__ code, LatticeParams p,
+                                   int form, const int64_t* __restrict__ cells, int n, double* __restrict__ out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t cell = cells[k];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) out[(int64_t)k * Q + i] = D3Q19::w(i) + (double)Storage<S>::load(A[i * ps + cell]);
+    for (int i = 0; i < Q; ++i) out[(int64_t)k * Q + i] = export_pop<S>(A, code, p, form, cell, i);
 }
 
 // ---------------------------------------------------------------------------
@@ -259,26 +282,33 @@ cudaError_t launch_classify(const uint8_t* flags, uint8_t* code, int nx, int ny,
 
 template <class S>
 static cudaError_t init_t(void* A, void* B, int64_t ps, const double* rho, const double* u, int64_t ustride,
-                          int64_t c0, int64_t count, cudaStream_t st) {
-    init_kernel<S><<<grid_for(count, 256), 256, 0, st>>>((S*)A, (S*)B, ps, rho, u, ustride, c0, count);
+                          int64_t c0, int64_t count, int swapped, cudaStream_t st) {
+    init_kernel<S><<<grid_for(count, 256), 256, 0, st>>>((S*)A, (S*)B, ps, rho, u, ustride, c0, count, swapped);
     return cudaGetLastError();
 }
 
 cudaError_t launch_init(int storage, void* A, void* B, int64_t ps, const double* rho, const double* u,
-                        int64_t ustride, int64_t c0, int64_t count, cudaStream_t st) {
-    LBGB_DISPATCH(storage, init_t<S>(A, B, ps, rho, u, ustride, c0, count, st));
+                        int64_t ustride, int64_t c0, int64_t count, cudaStream_t st, int swapped) {
+    LBGB_DISPATCH(storage, init_t<S>(A, B, ps, rho, u, ustride, c0, count, swapped, st));
 }
 
 template <class S>
 static cudaError_t moments_t(const void* A, const uint8_t* code, const LatticeParams& p, double* rho, double* u,
-                             int64_t ustride, int64_t c0, int64_t count, cudaStream_t st) {
-    moments_kernel<S><<<grid_for(count, 256), 256, 0, st>>>((const S*)A, code, p, rho, u, ustride, c0, count);
+                             int64_t ustride, int64_t c0, int64_t count, int form, cudaStream_t st) {
+    const int g = grid_for(count, 256);
+    const S* a = (const S*)A;
+    if (form == FORM_SWAPPED)
+        moments_kernel<S, FORM_SWAPPED><<<g, 256, 0, st>>>(a, code, p, rho, u, ustride, c0, count);
+    else if (form == FORM_STREAMED)
+        moments_kernel<S, FORM_STREAMED><<<g, 256, 0, st>>>(a, code, p, rho, u, ustride, c0, count);
+    else
+        moments_kernel<S, FORM_AB><<<g, 256, 0, st>>>(a, code, p, rho, u, ustride, c0, count);
     return cudaGetLastError();
 }
 
 cudaError_t launch_moments(int storage, const void* A, const uint8_t* code, const LatticeParams& p, double* rho,
-                           double* u, int64_t ustride, int64_t c0, int64_t count, cudaStream_t st) {
-    LBGB_DISPATCH(storage, moments_t<S>(A, code, p, rho, u, ustride, c0, count, st));
+                           double* u, int64_t ustride, int64_t c0, int64_t count, cudaStream_t st, int form) {
+    LBGB_DISPATCH(storage, moments_t<S>(A, code, p, rho, u, ustride, c0, count, form, st));
 }
 
 int totals_blocks(int64_t N) {
@@ -291,50 +321,58 @@ int totals_blocks(int64_t N) {
 
 template <class S>
 static cudaError_t totals_t(const void* A, const uint8_t* code, const LatticeParams& p, double* partials,
-                            double* out5, cudaStream_t st) {
+                            double* out5, int form, cudaStream_t st) {
     const int nb = totals_blocks(p.N);
-    totals_kernel<S><<<nb, TOT_THREADS, 0, st>>>((const S*)A, code, p, partials);
+    const S* a = (const S*)A;
+    if (form == FORM_SWAPPED)
+        totals_kernel<S, FORM_SWAPPED><<<nb, TOT_THREADS, 0, st>>>(a, code, p, partials);
+    else if (form == FORM_STREAMED)
+        totals_kernel<S, FORM_STREAMED><<<nb, TOT_THREADS, 0, st>>>(a, code, p, partials);
+    else
+        totals_kernel<S, FORM_AB><<<nb, TOT_THREADS, 0, st>>>(a, code, p, partials);
     totals_finalize_kernel<<<1, TOT_THREADS, 0, st>>>(partials, nb, p, out5);
     return cudaGetLastError();
 }
 
 cudaError_t launch_totals(int storage, const void* A, const uint8_t* code, const LatticeParams& p,
-                          double* partials, double* out5, cudaStream_t st) {
-    LBGB_DISPATCH(storage, totals_t<S>(A, code, p, partials, out5, st));
+                          double* partials, double* out5, cudaStream_t st, int form) {
+    LBGB_DISPATCH(storage, totals_t<S>(A, code, p, partials, out5, form, st));
 }
 
 template <class S>
-static cudaError_t get_pops_t(const void* A, int64_t ps, int64_t c0, int64_t count, double* buf, cudaStream_t st) {
-    get_pops_kernel<S><<<grid_for(count, 256), 256, 0, st>>>((const S*)A, ps, c0, count, buf);
+static cudaError_t get_pops_t(const void* A, const uint8_t* code, const LatticeParams& p, int form, int64_t c0,
+                              int64_t count, double* buf, cudaStream_t st) {
+    get_pops_kernel<S><<<grid_for(count, 256), 256, 0, st>>>((const S*)A, code, p, form, c0, count, buf);
     return cudaGetLastError();
 }
 
-cudaError_t launch_get_pops(int storage, const void* A, int64_t ps, int64_t c0, int64_t count, double* buf,
-                            cudaStream_t st) {
-    LBGB_DISPATCH(storage, get_pops_t<S>(A, ps, c0, count, buf, st));
+cudaError_t launch_get_pops(int storage, const void* A, const uint8_t* code, const LatticeParams& p, int form,
+                            int64_t c0, int64_t count, double* buf, cudaStream_t st) {
+    LBGB_DISPATCH(storage, get_pops_t<S>(A, code, p, form, c0, count, buf, st));
 }
 
 template <class S>
 static cudaError_t set_pops_t(void* A, void* B, int64_t ps, int64_t c0, int64_t count, const double* buf,
-                              cudaStream_t st) {
-    set_pops_kernel<S><<<grid_for(count, 256), 256, 0, st>>>((S*)A, (S*)B, ps, c0, count, buf);
+                              int swapped, cudaStream_t st) {
+    set_pops_kernel<S><<<grid_for(count, 256), 256, 0, st>>>((S*)A, (S*)B, ps, c0, count, buf, swapped);
     return cudaGetLastError();
 }
 
 cudaError_t launch_set_pops(int storage, void* A, void* B, int64_t ps, int64_t c0, int64_t count,
-                            const double* buf, cudaStream_t st) {
-    LBGB_DISPATCH(storage, set_pops_t<S>(A, B, ps, c0, count, buf, st));
+                            const double* buf, cudaStream_t st, int swapped) {
+    LBGB_DISPATCH(storage, set_pops_t<S>(A, B, ps, c0, count, buf, swapped, st));
 }
 
 template <class S>
-static cudaError_t gather_t(const void* A, int64_t ps, const int64_t* cells, int n, double* out, cudaStream_t st) {
-    gather_pops_kernel<S><<<(n + 127) / 128, 128, 0, st>>>((const S*)A, ps, cells, n, out);
+static cudaError_t gather_t(const void* A, const uint8_t* code, const LatticeParams& p, int form,
+                            const int64_t* cells, int n, double* out, cudaStream_t st) {
+    gather_pops_kernel<S><<<(n + 127) / 128, 128, 0, st>>>((const S*)A, code, p, form, cells, n, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather_pops(int storage, const void* A, int64_t ps, const int64_t* cells, int n, double* out,
-                               cudaStream_t st) {
-    LBGB_DISPATCH(storage, gather_t<S>(A, ps, cells, n, out, st));
+cudaError_t launch_gather_pops(int storage, const void* A, const uint8_t* code, const LatticeParams& p, int form,
+                               const int64_t* cells, int n, double* out, cudaStream_t st) {
+    LBGB_DISPATCH(storage, gather_t<S>(A, code, p, form, cells, n, out, st));
 }
 
 }  // namespace lbgb

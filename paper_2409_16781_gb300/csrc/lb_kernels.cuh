@@ -37,11 +37,28 @@ __device__ __forceinline__ void st_pop(S* p, S v) {
     }
 }
 
-// Streaming, pull form: d[i] <- A_i(x - c_i), with periodic wrap at the
+// Where the state between two steps keeps the post-collision value P_i(x)
+// of direction i at cell x:
+//   FORM_AB        plane i, cell x (the two-array scheme of Sec. 3.1: the
+//                  step reads array A and writes array B);
+//   FORM_SWAPPED   plane opp(i), cell x   (in-place "AA" scheme, after an
+//   FORM_STREAMED  plane i, cell x + c_i   even / odd number of steps).
+// The in-place scheme keeps one array: a step from FORM_SWAPPED reads the
+// values streaming into cell x from plane opp(i) at x - c_i and writes its
+// results to plane i at x + c_i (FORM_STREAMED); a step from FORM_STREAMED
+// reads plane i at x and writes plane opp(i) at x (FORM_SWAPPED).  Either
+// way a thread writes exactly the locations it read, so no two threads
+// touch the same value.  A fluid cell's value streaming into a solid
+// neighbour s = x + c_i lands in the solid cell's slot (plane i at s),
+// where the bounce-back of the next step finds it.
+enum { FORM_AB = 0, FORM_SWAPPED = 1, FORM_STREAMED = 2 };
+
+// Streaming, pull form: d[i] <- P_i(x - c_i), with periodic wrap at the
 // domain edges; if the source is a solid cell, halfway bounce-back takes the
-// cell's own opposite post-collision value, plus 6 w_i (c_i . u_lid) when
-// the source is a moving-lid cell (wall density 1).
-template <class S, int HINT = 0>
+// cell's own opposite post-collision value P_opp(i)(x), plus
+// 6 w_i (c_i . u_lid) when the source is a moving-lid cell (wall density 1).
+// FORM says where P lives (above).
+template <class S, int HINT = 0, int FORM = FORM_AB>
 __device__ __forceinline__ void pull_cell(const S* __restrict__ A, const uint8_t* __restrict__ code,
                                           const LatticeParams& p, int x, int y, int z, int cell,
                                           uint8_t cc, typename Storage<S>::math (&d)[Q]) {
@@ -52,11 +69,23 @@ __device__ __forceinline__ void pull_cell(const S* __restrict__ A, const uint8_t
     const int xs[3] = {x == nx - 1 ? 0 : x + 1, x, x == 0 ? nx - 1 : x - 1};
     const int ys[3] = {(y == ny - 1 ? 0 : y + 1) * nx, y * nx, (y == 0 ? ny - 1 : y - 1) * nx};
     const int zs[3] = {(z == nz - 1 ? 0 : z + 1) * nxy, z * nxy, (z == 0 ? nz - 1 : z - 1) * nxy};
+    // P_i at a fluid source src, and P_opp(i) at this cell (bounce-back)
+    auto fluid_src = [&](int i, int src) -> M {
+        if constexpr (FORM == FORM_AB) return Storage<S>::load(ld_pop<HINT>(A + (int64_t)i * p.ps + src));
+        else if constexpr (FORM == FORM_SWAPPED)
+            return Storage<S>::load(ld_pop<HINT>(A + (int64_t)D3Q19::opp(i) * p.ps + src));
+        else return Storage<S>::load(ld_pop<HINT>(A + (int64_t)i * p.ps + cell));
+    };
+    auto own_opp = [&](int i, int src) -> M {
+        if constexpr (FORM == FORM_AB) return Storage<S>::load(ld_pop<HINT>(A + (int64_t)D3Q19::opp(i) * p.ps + cell));
+        else if constexpr (FORM == FORM_SWAPPED) return Storage<S>::load(ld_pop<HINT>(A + (int64_t)i * p.ps + cell));
+        else return Storage<S>::load(ld_pop<HINT>(A + (int64_t)D3Q19::opp(i) * p.ps + src));
+    };
     if (!(cc & CODE_NEAR_WALL)) {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int src = xs[D3Q19::cx(i) + 1] + ys[D3Q19::cy(i) + 1] + zs[D3Q19::cz(i) + 1];
-            d[i] = Storage<S>::load(ld_pop<HINT>(A + (int64_t)i * p.ps + src));
+            d[i] = fluid_src(i, src);
         }
     } else {
 #pragma unroll
@@ -64,9 +93,9 @@ __device__ __forceinline__ void pull_cell(const S* __restrict__ A, const uint8_t
             const int src = xs[D3Q19::cx(i) + 1] + ys[D3Q19::cy(i) + 1] + zs[D3Q19::cz(i) + 1];
             const uint8_t t = (i == 0) ? 0 : (code[src] & CODE_TYPE);
             if (t == 0) {
-                d[i] = Storage<S>::load(ld_pop<HINT>(A + (int64_t)i * p.ps + src));
+                d[i] = fluid_src(i, src);
             } else {
-                M v = Storage<S>::load(ld_pop<HINT>(A + (int64_t)D3Q19::opp(i) * p.ps + cell));
+                M v = own_opp(i, src);
                 if (t == 2) {
                     const double cu = D3Q19::cx(i) * p.ulid[0] + D3Q19::cy(i) * p.ulid[1] +
                                       D3Q19::cz(i) * p.ulid[2];
@@ -130,12 +159,50 @@ __device__ __forceinline__ void moment_sums(const M (&d)[Q], M& drho, M& jx, M& 
     drho = s;
 }
 
+// Two cells' FP32 values in one register pair.  Arithmetic on it maps to the
+// packed FP32 instructions of sm_100-class GPUs (add / mul / fma on .f32x2:
+// one instruction for both cells, each lane rounded exactly as the scalar
+// instruction would round it).  The step kernels that keep two x-adjacent
+// cells per register pair run the same collision template on it.
+struct f32x2 {
+    float2 v;
+    f32x2() = default;
+    __device__ __forceinline__ f32x2(int s) : v(make_float2((float)s, (float)s)) {}
+    __device__ __forceinline__ f32x2(float s) : v(make_float2(s, s)) {}
+    __device__ __forceinline__ explicit f32x2(double s) : v(make_float2((float)s, (float)s)) {}
+    __device__ __forceinline__ f32x2(float a, float b) : v(make_float2(a, b)) {}
+};
+__device__ __forceinline__ f32x2 operator+(f32x2 a, f32x2 b) {
+    f32x2 r;
+    r.v = __fadd2_rn(a.v, b.v);
+    return r;
+}
+__device__ __forceinline__ f32x2 operator-(f32x2 a) { return f32x2(-a.v.x, -a.v.y); }
+__device__ __forceinline__ f32x2 operator-(f32x2 a, f32x2 b) { return a + (-b); }
+__device__ __forceinline__ f32x2 operator*(f32x2 a, f32x2 b) {
+    f32x2 r;
+    r.v = __fmul2_rn(a.v, b.v);
+    return r;
+}
+__device__ __forceinline__ f32x2& operator+=(f32x2& a, f32x2 b) { return a = a + b; }
+__device__ __forceinline__ f32x2& operator-=(f32x2& a, f32x2 b) { return a = a - b; }
+
+// Fused multiply-add a * b + c (one rounding) for every math type.
+__device__ __forceinline__ double fmad(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ f32x2 fmad(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 r;
+    r.v = __ffma2_rn(a.v, b.v, c.v);
+    return r;
+}
+
 // 1/rho, correctly rounded.  An approximate reciprocal is not good enough:
 // its error has a sign bias, so the equilibrium momentum rho u falls short
 // of j by a fixed fraction every step and the collision drains momentum
 // (an artificial dissipation that builds up over thousands of steps).
 __device__ __forceinline__ double recip(double r) { return 1.0 / r; }
 __device__ __forceinline__ float recip(float r) { return __frcp_rn(r); }
+__device__ __forceinline__ f32x2 recip(f32x2 r) { return f32x2(__frcp_rn(r.v.x), __frcp_rn(r.v.y)); }
 
 // Density and half-force-shifted velocity u = j/rho + g/2 from deviations.
 template <class M>
@@ -145,9 +212,9 @@ __device__ __forceinline__ void macro_dev(const M (&d)[Q], const LatticeParams& 
     moment_sums<M>(d, drho, jx, jy, jz);
     rho = M(1) + drho;
     const M inv = recip(rho);
-    ux = jx * inv + M(0.5) * (M)p.g[0];
-    uy = jy * inv + M(0.5) * (M)p.g[1];
-    uz = jz * inv + M(0.5) * (M)p.g[2];
+    ux = fmad(jx, inv, M(0.5) * (M)p.g[0]);
+    uy = fmad(jy, inv, M(0.5) * (M)p.g[1]);
+    uz = fmad(jz, inv, M(0.5) * (M)p.g[2]);
 }
 
 // BGK relaxation towards f^eq (Eq. 2-3) plus the Guo source term (the S_i
@@ -164,8 +231,22 @@ __device__ __forceinline__ void macro_dev(const M (&d)[Q], const LatticeParams& 
 // three axis pairs take the difference that makes the momentum exactly
 // j + F, and the rest population the value that keeps the mass: the same
 // collision, with the conservation laws holding to rounding.
-template <class M, bool FORCE>
-__device__ __forceinline__ void relax_dev(M (&d)[Q], const LatticeParams& p) {
+//
+// Two-relaxation-time form (Ginzburg's TRT; not in the paper): the pair
+// differences (odd part) relax at p.omega_m and take the odd Guo part scaled
+// by (1 - omega_m/2); the pair sums (even part) keep omega.  omega_m = omega
+// is the BGK collision above, evaluated by the same expressions.  The
+// momentum j + F after the collision holds for any omega_m.
+//
+// M is double, float, or f32x2 (two cells at once); every multiply-add is an
+// explicit fmad, so the packed form rounds each cell as the scalar form does.
+//
+// relax_emit hands each post-collision value to emit(i, value) as soon as it
+// is final (the diagonal pairs first, then the axis pairs, then the rest
+// population), so a kernel can store it at once instead of keeping all 19
+// in registers; relax_dev writes them back into d.
+template <class M, bool FORCE, class Emit>
+__device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams& p, Emit&& emit) {
     // pre-collision pair sums / differences and moments
     M ps[9], pd[9];
     M drho = d[0], jx = 0, jy = 0, jz = 0;
@@ -184,80 +265,115 @@ __device__ __forceinline__ void relax_dev(M (&d)[Q], const LatticeParams& p) {
     }
     const M rho = M(1) + drho;
     const M inv = recip(rho);
-    const M ux = jx * inv + M(0.5) * (M)p.g[0];
-    const M uy = jy * inv + M(0.5) * (M)p.g[1];
-    const M uz = jz * inv + M(0.5) * (M)p.g[2];
+    const M ux = fmad(jx, inv, M(0.5) * (M)p.g[0]);
+    const M uy = fmad(jy, inv, M(0.5) * (M)p.g[1]);
+    const M uz = fmad(jz, inv, M(0.5) * (M)p.g[2]);
     const M om = (M)p.omega;
-    const M omc = M(1) - om;
-    const M uu15 = M(1.5) * (ux * ux + uy * uy + uz * uz);
-    M Fx = 0, Fy = 0, Fz = 0, uF = 0, pref = 0;
+    const M omm = (M)p.omega_m;
+    const M uu15 = M(1.5) * fmad(ux, ux, fmad(uy, uy, uz * uz));
+    M Fx = 0, Fy = 0, Fz = 0, uF = 0, pref = 0, pref_m = 0;
     if (FORCE) {
         Fx = rho * (M)p.g[0];
         Fy = rho * (M)p.g[1];
         Fz = rho * (M)p.g[2];
-        uF = ux * Fx + uy * Fy + uz * Fz;
-        pref = M(1) - M(0.5) * om;
+        uF = fmad(ux, Fx, fmad(uy, Fy, uz * Fz));
+        pref = fmad(M(-0.5), om, M(1));
+        pref_m = fmad(M(-0.5), omm, M(1));
     }
     // Half the post-collision pair sums (hs) and differences (hd):
-    //   hs = (1 - omega)/2 (d_i + d_i') + even,   hd = (1 - omega)/2 (d_i - d_i') + odd,
+    //   hs = (1 - omega)/2 (d_i + d_i') + even,   hd = (1 - omega_m)/2 (d_i - d_i') + odd,
     //   d_i = hs + hd,  d_i' = hs - hd,  per weight class W:
     //   even = omega W (rho (4.5 cu^2 - 1.5 uu) + drho) [+ pref W (9 cu cF - 3 uF)]
-    //   odd  = 3 omega W rho cu                         [+ 3 pref W cF]
+    //   odd  = 3 omega_m W rho cu                       [+ 3 pref_m W cF]
     const M wa = (M)D3Q19::w(1), wb = (M)D3Q19::w(7);
-    const M omh = M(0.5) * omc;
+    const M omh = fmad(M(-0.5), om, M(0.5));
+    const M omh_m = fmad(M(-0.5), omm, M(0.5));
     const M orho = om * rho;
-    const M base = om * (drho - rho * uu15);
+    const M base = om * fmad(rho, -uu15, drho);
     const M a1 = M(4.5) * wa * orho, b1 = wa * base;
-    const M a2 = M(4.5) * wb * orho, b2 = wb * base, c2 = M(3) * wb * orho;
+    const M a2 = M(4.5) * wb * orho, b2 = wb * base, c2 = M(3) * wb * (omm * rho);
     M fa1 = 0, fb1 = 0, fa2 = 0, fb2 = 0, fc2 = 0;
     if (FORCE) {
         fa1 = M(9) * pref * wa;
         fb1 = M(-3) * pref * wa * uF;
         fa2 = M(9) * pref * wb;
         fb2 = M(-3) * pref * wb * uF;
-        fc2 = M(3) * pref * wb;
+        fc2 = M(3) * pref_m * wb;
     }
-    M hs[9], hd[9];
+    // c_i . u and c_i . F of the pair (2k+1, 2k+2): a signed component for an
+    // axis pair, the sum or difference of two components for a diagonal pair
+    auto dot = [&](int i, M& cu, M& cF) {
+        bool first = true;
+        auto term = [&](int c, M u, M F) {
+            if (c == 0) return;
+            if (first) {
+                cu = c > 0 ? u : -u;
+                cF = c > 0 ? F : -F;
+                first = false;
+            } else if (c > 0) {
+                cu = cu + u;
+                cF = cF + F;
+            } else {
+                cu = cu - u;
+                cF = cF - F;
+            }
+        };
+        term(D3Q19::cx(i), ux, Fx);
+        term(D3Q19::cy(i), uy, Fy);
+        term(D3Q19::cz(i), uz, Fz);
+    };
+    // the even half-sums of the axis pairs (needed for the mass below)
+    M hsa[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        M cu = 0, cF = 0;
+        dot(2 * k + 1, cu, cF);
+        M even = fmad(a1, cu * cu, b1);
+        if (FORCE) even = even + fmad(fa1, cu * cF, fb1);
+        hsa[k] = fmad(omh, ps[k], even);
+    }
+    M msum = hsa[0] + hsa[1] + hsa[2];
     M ox = 0, oy = 0, oz = 0;  // half the momentum carried by the 12 diagonal directions
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
+    for (int k = 3; k < 9; ++k) {
         const int i = 2 * k + 1;
-        const bool axis = k < 3;
         M cu = 0, cF = 0;
-        if (D3Q19::cx(i) == 1) { cu += ux; cF += Fx; }
-        if (D3Q19::cx(i) == -1) { cu -= ux; cF -= Fx; }
-        if (D3Q19::cy(i) == 1) { cu += uy; cF += Fy; }
-        if (D3Q19::cy(i) == -1) { cu -= uy; cF -= Fy; }
-        if (D3Q19::cz(i) == 1) { cu += uz; cF += Fz; }
-        if (D3Q19::cz(i) == -1) { cu -= uz; cF -= Fz; }
-        M even = (axis ? a1 : a2) * (cu * cu) + (axis ? b1 : b2);
-        if (FORCE) even += (axis ? fa1 : fa2) * (cu * cF) + (axis ? fb1 : fb2);
-        hs[k] = omh * ps[k] + even;
-        if (!axis) {
-            M odd = c2 * cu;
-            if (FORCE) odd += fc2 * cF;
-            hd[k] = omh * pd[k] + odd;
-            if (D3Q19::cx(i) == 1) ox += hd[k];
-            if (D3Q19::cx(i) == -1) ox -= hd[k];
-            if (D3Q19::cy(i) == 1) oy += hd[k];
-            if (D3Q19::cy(i) == -1) oy -= hd[k];
-            if (D3Q19::cz(i) == 1) oz += hd[k];
-            if (D3Q19::cz(i) == -1) oz -= hd[k];
-        }
+        dot(i, cu, cF);
+        M even = fmad(a2, cu * cu, b2);
+        if (FORCE) even = even + fmad(fa2, cu * cF, fb2);
+        const M hs = fmad(omh, ps[k], even);
+        M odd = c2 * cu;
+        if (FORCE) odd = fmad(fc2, cF, odd);
+        const M hd = fmad(omh_m, pd[k], odd);
+        if (D3Q19::cx(i) == 1) ox += hd;
+        if (D3Q19::cx(i) == -1) ox -= hd;
+        if (D3Q19::cy(i) == 1) oy += hd;
+        if (D3Q19::cy(i) == -1) oy -= hd;
+        if (D3Q19::cz(i) == 1) oz += hd;
+        if (D3Q19::cz(i) == -1) oz -= hd;
+        msum += hs;
+        emit(i, hs + hd);
+        emit(i + 1, hs - hd);
     }
     // axis pairs (1,2) x, (3,4) y, (5,6) z: post-collision momentum j + F
-    hd[0] = M(0.5) * (jx + Fx) - ox;
-    hd[1] = M(0.5) * (jy + Fy) - oy;
-    hd[2] = M(0.5) * (jz + Fz) - oz;
-    M msum = 0;
+    const M hdx = fmad(M(0.5), jx + Fx, -ox);
+    const M hdy = fmad(M(0.5), jy + Fy, -oy);
+    const M hdz = fmad(M(0.5), jz + Fz, -oz);
+    emit(1, hsa[0] + hdx);
+    emit(2, hsa[0] - hdx);
+    emit(3, hsa[1] + hdy);
+    emit(4, hsa[1] - hdy);
+    emit(5, hsa[2] + hdz);
+    emit(6, hsa[2] - hdz);
+    emit(0, fmad(M(-2), msum, drho));  // mass unchanged by the collision
+}
+
+template <class M, bool FORCE>
+__device__ __forceinline__ void relax_dev(M (&d)[Q], const LatticeParams& p) {
+    M out[Q];
+    relax_emit<M, FORCE>(d, p, [&](int i, M v) { out[i] = v; });
 #pragma unroll
-    for (int k = 0; k < 9; ++k) msum += hs[k];
-    d[0] = drho - M(2) * msum;  // mass unchanged by the collision
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        d[2 * k + 1] = hs[k] + hd[k];
-        d[2 * k + 2] = hs[k] - hd[k];
-    }
+    for (int i = 0; i < Q; ++i) d[i] = out[i];
 }
 
 }  // namespace lbgb

@@ -181,6 +181,7 @@ extern "C" int lb_totals_static(const void* populations, int64_t plane_stride, c
     p.N = N;
     p.ps = plane_stride;
     p.omega = 1.0;  // not used by the totals
+    p.omega_m = 1.0;
     p.err = nullptr;
     for (int a = 0; a < 3; ++a) {
         p.g[a] = force ? force[a] : 0.0;

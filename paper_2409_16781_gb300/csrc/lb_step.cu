@@ -394,6 +394,218 @@ static cudaError_t step_quads16_t(const void* A, void* B, const uint8_t* code, c
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Variants 13 and 14: the collision of two x-adjacent cells at once in packed
+// FP32 (f32x2: one add/mul/fma instruction for both cells), which halves the
+// arithmetic instructions per cell -- the bound of the 16-bit kernels, whose
+// bytes per cell are half those of FP32 storage.
+//   13: two cells per thread (float, FP16 or BF16 storage, nx even); each
+//       direction is one aligned 2-vector load, x-shifts by lane shuffles as
+//       in variant 4.
+//   14: four cells per thread (16-bit storage, nx % 4 == 0); one 8-byte load
+//       per direction as in variant 8, the cells collided as two pairs.
+// Cells next to a wall leave the packed form for the bounce-back fix-up of
+// each cell and re-enter it.
+// ---------------------------------------------------------------------------
+template <class S> __device__ __forceinline__ f32x2 to_x2(uint32_t w);  // two packed 16-bit values
+template <> __device__ __forceinline__ f32x2 to_x2<__half>(uint32_t w) {
+    f32x2 r;
+    r.v = __half22float2(*reinterpret_cast<const __half2*>(&w));
+    return r;
+}
+template <> __device__ __forceinline__ f32x2 to_x2<__nv_bfloat16>(uint32_t w) {
+    return f32x2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+template <class S> __device__ __forceinline__ uint32_t from_x2(f32x2 d);
+template <> __device__ __forceinline__ uint32_t from_x2<__half>(f32x2 d) {
+    const __half2 h = __float22half2_rn(d.v);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+template <> __device__ __forceinline__ uint32_t from_x2<__nv_bfloat16>(f32x2 d) {
+    const __nv_bfloat162 h = __float22bfloat162_rn(d.v);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Bounce-back fix-up of the cells of a packed pair whose codes say so.
+template <class S, int HINT>
+__device__ __forceinline__ void bounce_fix_x2(const S* __restrict__ A, const uint8_t* __restrict__ code,
+                                              const LatticeParams& p, int x0, int y, int z, int cell0, uint8_t c0,
+                                              uint8_t c1, f32x2 (&d)[Q]) {
+    if (!((c0 | c1) & CODE_NEAR_WALL)) return;
+    float a[Q], b[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        a[i] = d[i].v.x;
+        b[i] = d[i].v.y;
+    }
+    if (c0 & CODE_NEAR_WALL) bounce_fix<S, HINT>(A, code, p, x0, y, z, cell0, a);
+    if (c1 & CODE_NEAR_WALL) bounce_fix<S, HINT>(A, code, p, x0 + 1, y, z, cell0 + 1, b);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) d[i] = f32x2(a[i], b[i]);
+}
+
+template <class S, bool FORCE, int HINT>
+__global__ void __launch_bounds__(256) step_kernel_pairs_x2(const S* __restrict__ A, S* __restrict__ B,
+                                                            const uint8_t* __restrict__ code, LatticeParams p,
+                                                            int xblocks) {
+    using V = typename Vec2<S>::T;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int xb = blockIdx.x % xblocks;
+    const int row = blockIdx.x / xblocks;
+    const int y = row % ny;
+    const int z = row / ny;
+    const int x0 = 2 * (xb * blockDim.x + threadIdx.x);
+    const bool active = x0 < nx;
+    const int xa = active ? x0 : 0;  // in-bounds address for idle lanes
+    const int lane = threadIdx.x & 31;
+    const int nxy = nx * ny;
+    const int yo[3] = {(y == ny - 1 ? 0 : y + 1) * nx, y * nx, (y == 0 ? ny - 1 : y - 1) * nx};
+    const int zo[3] = {(z == nz - 1 ? 0 : z + 1) * nxy, z * nxy, (z == 0 ? nz - 1 : z - 1) * nxy};
+    const int cell0 = xa + nx * row;
+    f32x2 d[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const S* rowp = A + (int64_t)i * p.ps + yo[D3Q19::cy(i) + 1] + zo[D3Q19::cz(i) + 1];
+        const V v = ld_pop<HINT>(reinterpret_cast<const V*>(rowp + xa));
+        float a, b;
+        split2<S>(v, a, b);
+        if (D3Q19::cx(i) == 0) {
+            d[i] = f32x2(a, b);
+        } else if (D3Q19::cx(i) == 1) {  // source x - 1
+            float prev = __shfl_up_sync(0xffffffffu, b, 1);
+            if (lane == 0 && active) prev = Storage<S>::load(ld_pop<HINT>(rowp + (x0 == 0 ? nx - 1 : x0 - 1)));
+            d[i] = f32x2(prev, a);
+        } else {  // source x + 1
+            float next = __shfl_down_sync(0xffffffffu, a, 1);
+            if (active && (lane == 31 || x0 + 2 >= nx))
+                next = Storage<S>::load(ld_pop<HINT>(rowp + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2)));
+            d[i] = f32x2(b, next);
+        }
+    }
+    if (!active) return;
+    const uint8_t c0 = code[cell0], c1 = code[cell0 + 1];
+    bounce_fix_x2<S, HINT>(A, code, p, x0, y, z, cell0, c0, c1, d);
+    relax_dev<f32x2, FORCE>(d, p);
+    const bool f0 = !(c0 & CODE_TYPE), f1 = !(c1 & CODE_TYPE);
+    if (f0 && f1) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            st_pop<HINT>(reinterpret_cast<V*>(B + (int64_t)i * p.ps + cell0), pack2<S>(d[i].v.x, d[i].v.y));
+    } else {  // solid cells are never written
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (f0) st_pop<HINT>(B + (int64_t)i * p.ps + cell0, Storage<S>::store(d[i].v.x));
+            if (f1) st_pop<HINT>(B + (int64_t)i * p.ps + cell0 + 1, Storage<S>::store(d[i].v.y));
+        }
+    }
+}
+
+template <class S, int HINT>
+static cudaError_t step_pairs_x2_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p, int block,
+                                   cudaStream_t st) {
+    int bx = block > 0 ? (block / 32) * 32 : 64;  // whole warps (the shuffles need all 32 lanes)
+    if (bx < 32) bx = 32;
+    if (bx > 256) bx = 256;
+    const int pairs = p.nx / 2;
+    const int need = ((pairs + 31) / 32) * 32;
+    if (bx > need) bx = need;
+    const int xblocks = (pairs + bx - 1) / bx;
+    const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
+    const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
+    if (force)
+        step_kernel_pairs_x2<S, true, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+    else
+        step_kernel_pairs_x2<S, false, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+    return cudaGetLastError();
+}
+
+template <class S, bool FORCE, int HINT>
+__global__ void __launch_bounds__(128, 4) step_kernel_quads16_x2(const S* __restrict__ A, S* __restrict__ B,
+                                                                 const uint8_t* __restrict__ code, LatticeParams p,
+                                                                 int xblocks) {
+    static_assert(sizeof(S) == 2, "16-bit storage only");
+    const uint16_t* __restrict__ A16 = reinterpret_cast<const uint16_t*>(A);
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int xb = blockIdx.x % xblocks;
+    const int row = blockIdx.x / xblocks;
+    const int y = row % ny;
+    const int z = row / ny;
+    const int x0 = 4 * (xb * blockDim.x + threadIdx.x);
+    const bool active = x0 < nx;
+    const int xa = active ? x0 : 0;  // in-bounds address for idle lanes
+    const int lane = threadIdx.x & 31;
+    const int nxy = nx * ny;
+    const int yo[3] = {(y == ny - 1 ? 0 : y + 1) * nx, y * nx, (y == 0 ? ny - 1 : y - 1) * nx};
+    const int zo[3] = {(z == nz - 1 ? 0 : z + 1) * nxy, z * nxy, (z == 0 ? nz - 1 : z - 1) * nxy};
+    const int cell0 = xa + nx * row;
+    uint2 v[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const uint16_t* rowp = A16 + (int64_t)i * p.ps + yo[D3Q19::cy(i) + 1] + zo[D3Q19::cz(i) + 1];
+        const uint2 raw = ld_pop<HINT>(reinterpret_cast<const uint2*>(rowp + xa));
+        if (D3Q19::cx(i) == 0) {
+            v[i] = raw;
+        } else if (D3Q19::cx(i) == 1) {  // source x - 1: (prev top, x0, x0+1, x0+2)
+            uint32_t prev = __shfl_up_sync(0xffffffffu, raw.y, 1);
+            if (lane == 0 && active)
+                prev = (uint32_t)ld_pop<HINT>(rowp + (x0 == 0 ? nx - 1 : x0 - 1)) << 16;
+            v[i] = make_uint2(__byte_perm(prev, raw.x, 0x5432), __byte_perm(raw.x, raw.y, 0x5432));
+        } else {  // source x + 1: (x0+1, x0+2, x0+3, next bottom)
+            uint32_t next = __shfl_down_sync(0xffffffffu, raw.x, 1);
+            if (active && (lane == 31 || x0 + 4 >= nx))
+                next = (uint32_t)ld_pop<HINT>(rowp + (x0 + 4 >= nx ? x0 + 4 - nx : x0 + 4));
+            v[i] = make_uint2(__byte_perm(raw.x, raw.y, 0x5432), __byte_perm(raw.y, next, 0x5432));
+        }
+    }
+    if (!active) return;
+    const uint32_t codes = *reinterpret_cast<const uint32_t*>(code + cell0);  // 4 code bytes
+    uint16_t* B16 = reinterpret_cast<uint16_t*>(B);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {  // cells (x0, x0+1), then (x0+2, x0+3)
+        const uint8_t ca = (uint8_t)(codes >> (16 * h)), cb = (uint8_t)(codes >> (16 * h + 8));
+        f32x2 d[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) d[i] = to_x2<S>(h == 0 ? v[i].x : v[i].y);
+        bounce_fix_x2<S, HINT>(A, code, p, x0 + 2 * h, y, z, cell0 + 2 * h, ca, cb, d);
+        relax_dev<f32x2, FORCE>(d, p);
+        // each pair is stored as soon as it is done (one 4-byte word per
+        // direction), so no packed results are held across the second pair.
+        // (Storing each value from inside the collision, as it becomes
+        // final, measured slower here.)
+        uint16_t* cp = B16 + cell0 + 2 * h;
+        if (!((ca | cb) & CODE_TYPE)) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) st_pop<HINT>(reinterpret_cast<uint32_t*>(cp + (int64_t)i * p.ps), from_x2<S>(d[i]));
+        } else {  // solid cells are never written
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const uint32_t word = from_x2<S>(d[i]);
+                if (!(ca & CODE_TYPE)) st_pop<HINT>(cp + (int64_t)i * p.ps, (uint16_t)(word & 0xffffu));
+                if (!(cb & CODE_TYPE)) st_pop<HINT>(cp + (int64_t)i * p.ps + 1, (uint16_t)(word >> 16));
+            }
+        }
+    }
+}
+
+template <class S, int HINT>
+static cudaError_t step_quads16_x2_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p, int block,
+                                     cudaStream_t st) {
+    int bx = block > 0 ? (block / 32) * 32 : 64;  // whole warps (the shuffles need all 32 lanes)
+    if (bx < 32) bx = 32;
+    if (bx > 128) bx = 128;
+    const int quads = p.nx / 4;
+    const int need = ((quads + 31) / 32) * 32;
+    if (bx > need) bx = need;
+    const int xblocks = (quads + bx - 1) / bx;
+    const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
+    const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
+    if (force)
+        step_kernel_quads16_x2<S, true, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+    else
+        step_kernel_quads16_x2<S, false, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+    return cudaGetLastError();
+}
+
 template <class S, int HINT>
 static cudaError_t step_rows_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p, int block,
                                cudaStream_t st);
@@ -816,12 +1028,22 @@ static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* co
                        : variant == 11 ? step_tma16_t<S, 2>(A, B, code, p, block, st)
                                        : step_tma16_t<S, 1>(A, B, code, p, block, st);
             return step_rows_t<S, 0>(A, B, code, p, block, st);
+        case 13:
+            if constexpr (std::is_same<S, float>::value || sizeof(S) == 2) {
+                if (pairs_ok) return step_pairs_x2_t<S, 0>(A, B, code, p, block, st);
+            }
+            return step_rows_t<S, 0>(A, B, code, p, block, st);
+        case 14:
+            if constexpr (sizeof(S) == 2) {
+                if (p.nx % 4 == 0) return step_quads16_x2_t<S, 0>(A, B, code, p, block, st);
+            }
+            return step_rows_t<S, 0>(A, B, code, p, block, st);
         case 0:
             // measured defaults on GB300 (256^3): FP32 one cell per thread in
             // 64-thread blocks; FP64 two cells per thread; 16-bit storage four
-            // cells per thread in packed registers
+            // cells per thread collided as packed FP32 pairs
             if constexpr (sizeof(S) == 2) {
-                if (p.nx % 4 == 0) return step_quads16_t<S, 0>(A, B, code, p, block > 0 ? block : 64, st);
+                if (p.nx % 4 == 0) return step_quads16_x2_t<S, 0>(A, B, code, p, block > 0 ? block : 32, st);
                 if (pairs_ok) return step_pairs16_t<S, 0>(A, B, code, p, block > 0 ? block : 64, st);
             }
             if constexpr (sizeof(S) == 8) {

@@ -29,20 +29,23 @@ def velocity_set():
     return c.reshape(19, 3).astype(np.int64), w
 
 
-def make_options(storage="f32", force=(0.0, 0.0, 0.0), stream=None, kernel=0, block=0):
+def make_options(storage="f32", force=(0.0, 0.0, 0.0), stream=None, kernel=0, block=0, trt_magic=0.0,
+                 inplace=False):
     o = L.LbOptions()
     L.lib().lb_default_options(ctypes.byref(o))
     o.storage = L.STORAGE[storage] if isinstance(storage, str) else int(storage)
     o.kernel = int(kernel)
     o.block = int(block)
+    o.trt_magic = float(trt_magic)
+    o.inplace = 1 if inplace else 0
     for a in range(3):
         o.force[a] = float(force[a])
     o.stream = stream
     return o
 
 
-def bytes_required(nx, ny, nz, storage="f32") -> int:
-    o = make_options(storage)
+def bytes_required(nx, ny, nz, storage="f32", inplace=False) -> int:
+    o = make_options(storage, inplace=inplace)
     return int(L.lib().lb_bytes_required(int(nx), int(ny), int(nz), ctypes.byref(o)))
 
 
@@ -52,11 +55,14 @@ class Lattice:
     Arrays follow the library's layout: scalar fields (nz, ny, nx), vector
     fields (3, nz, ny, nx), populations (19, nz, ny, nx) in the library's
     velocity order; flags uint8 (nz, ny, nx) with 0 fluid, 1 wall, 2 lid.
+    trt_magic: 0 = BGK collision; > 0 = two-relaxation-time collision with
+    that magic parameter (lb_options.trt_magic).
+    inplace: one population array updated in place (lb_options.inplace).
     """
 
     def __init__(self, nx, ny, nz, tau, u_lid=(0.0, 0.0, 0.0), flags=None, storage="f32",
                  force=(0.0, 0.0, 0.0), device=None, stream=None, kernel=0, block=0,
-                 library_memory=False):
+                 library_memory=False, trt_magic=0.0, inplace=False):
         import torch
 
         self.lib = L.lib()
@@ -70,7 +76,10 @@ class Lattice:
         if stream is None:
             stream = torch.cuda.current_stream(self.device)
         self.stream = stream
-        opts = make_options(storage, force, ctypes.c_void_p(stream.cuda_stream), kernel, block)
+        opts = make_options(storage, force, ctypes.c_void_p(stream.cuda_stream), kernel, block, trt_magic,
+                            inplace)
+        self.trt_magic = float(trt_magic)
+        self.inplace = bool(inplace)
         ulid = (ctypes.c_double * 3)(*[float(v) for v in u_lid])
         fl = None
         if flags is not None:
@@ -190,7 +199,8 @@ class Lattice:
         ~/.cache/lbgb/autotune.json).  Returns (variant, block, ms/step)."""
         import torch
         key = "|".join([torch.cuda.get_device_name(self.device), str(self.storage),
-                        f"{self.nx}x{self.ny}x{self.nz}", "force" if self._force else "noforce"])
+                        f"{self.nx}x{self.ny}x{self.nz}", "force" if self._force else "noforce"]
+                       + (["trt"] if self.trt_magic else []) + (["inplace"] if self.inplace else []))
         path = os.environ.get("LBGB_AUTOTUNE_CACHE",
                               os.path.join(os.path.expanduser("~"), ".cache", "lbgb", "autotune.json"))
         table = {}

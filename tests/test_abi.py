@@ -99,3 +99,38 @@ def test_null_handle_calls(lib):
     assert lib.lb_moments(None, None, None) == L.LB_EINVAL
     assert lib.lb_destroy(None) == L.LB_OK
     assert lib.lb_status_string(L.LB_EDIVERGED) == b"simulation diverged"
+
+
+def test_options_layout_and_trt_validation(lib):
+    """lb_options keeps its 80-byte layout; a negative or non-finite TRT
+    magic parameter is rejected before any device work."""
+    assert ctypes.sizeof(L.LbOptions) == 80
+    assert L.LbOptions.trt_magic.offset == 48
+    assert L.LbOptions.inplace.offset == 56
+    for bad in (-0.1, float("nan"), float("inf")):
+        o = L.LbOptions()
+        lib.lb_default_options(ctypes.byref(o))
+        assert o.trt_magic == 0.0
+        o.trt_magic = bad
+        h = ctypes.c_void_p()
+        st = lib.lb_create(ctypes.byref(h), 4, 4, 4, 0.7, None, None, ctypes.byref(o))
+        assert st == L.LB_EINVAL
+        assert "trt_magic" in lib.lb_last_error().decode()
+
+
+def test_inplace_option(lib):
+    """One population array halves the population memory; inplace must be
+    0 or 1."""
+    from paper_2409_16781_gb300 import bytes_required
+    two = bytes_required(128, 128, 128, "f32")
+    one = bytes_required(128, 128, 128, "f32", inplace=True)
+    pops = 19 * 128 ** 3 * 4
+    assert two - one == pops
+    o = L.LbOptions()
+    lib.lb_default_options(ctypes.byref(o))
+    assert o.inplace == 0
+    o.inplace = 2
+    assert lib.lb_bytes_required(8, 8, 8, ctypes.byref(o)) == 0
+    h = ctypes.c_void_p()
+    assert lib.lb_create(ctypes.byref(h), 8, 8, 8, 0.7, None, None, ctypes.byref(o)) == L.LB_EINVAL
+    assert "inplace" in lib.lb_last_error().decode()

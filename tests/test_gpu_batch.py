@@ -104,6 +104,29 @@ def test_batch_matches_oracle_f64():
     b.close()
 
 
+def test_batch_trt_matches_oracle():
+    """Slots with the two-relaxation-time collision (per-slot magic
+    parameter) next to a BGK slot, against the oracle's TRT / BGK steps."""
+    perm = lib_to_oracle_perm()
+    b = Batch(capacity_bytes=16 << 20, max_slots=4)
+    cases = [(11, 9, 7, 0.52, "cavity", 30, 3 / 16), (16, 6, 10, 0.8, "random", 19, 1 / 4),
+             (12, 8, 6, 0.7, "channel", 25, 0.0)]
+    slots = []
+    for nx, ny, nz, tau, kind, steps, magic in cases:
+        flags, ulid, g = _geom(nx, ny, nz, kind)
+        slots.append(b.add(nx, ny, nz, tau, steps, u_lid=ulid, flags=flags, storage="f64", force=g,
+                           trt_magic=magic))
+    b.step(31)
+    for s, (nx, ny, nz, tau, kind, steps, magic) in zip(slots, cases):
+        flags, ulid, g = _geom(nx, ny, nz, kind)
+        om = O.trt_omega_minus(tau, magic) if magic else None
+        ora = O.Lattice(nx, ny, nz, tau, u_lid=ulid, flags=flags, force=g, omega_minus=om)
+        ora.step(steps)
+        err = pop_rel_err(b.populations(s), to_lib_order(ora.A, perm), fluid_mask(flags, (nz, ny, nx)))
+        assert err <= 1e-12
+    b.close()
+
+
 def test_graph_path_and_init_fields():
     """Step counts above the graph size (8) replay captured graphs; the
     result equals the single-lattice run."""
