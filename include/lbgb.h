@@ -235,8 +235,10 @@ int lb_totals_static(const void *populations, int64_t plane_stride, const uint8_
  * ------------------------------------------------------------------- */
 typedef struct lb_batch lb_batch; /* opaque */
 
-/* Pool bytes one slot of this size and storage takes (0 on bad sizes). */
-size_t lb_batch_slot_bytes(int nx, int ny, int nz, int storage);
+/* Pool bytes one slot of this size, storage and population layout
+ * (inplace 0: two arrays, 1: one array, as lb_options.inplace) takes (0 on
+ * bad arguments). */
+size_t lb_batch_slot_bytes(int nx, int ny, int nz, int storage, int inplace);
 /* Device bytes of a batch's fixed area (slot table, work lists, reduction
  * scratch, 16 MiB host-transfer staging) for max_slots slots. */
 size_t lb_batch_fixed_bytes(int max_slots);
@@ -251,8 +253,11 @@ int lb_batch_create(lb_batch **out, size_t capacity_bytes, int max_slots, void *
  * (256-byte aligned; the pool is what remains after the fixed area). */
 int lb_batch_create_in(lb_batch **out, void *device_buffer, size_t bytes, int max_slots, void *stream);
 
-/* Admit a lattice: arguments as lb_create (opt: storage and force), plus
- * the number of steps it is to take.  Starts at rest (f = w).  Returns the
+/* Admit a lattice: arguments as lb_create (opt: storage, force, trt_magic
+ * and inplace -- an in-place slot keeps one population array, so the pool
+ * holds about twice as many; its lb_batch_fetch reads back through the
+ * batch's staging area instead of the slot's spare array), plus the number
+ * of steps it is to take.  Starts at rest (f = w).  Returns the
  * slot id in *slot.  LB_ENOMEM: it does not fit the pool's free space;
  * LB_EBUSY: all slots in use; LB_EINVAL: bad arguments.  Synchronises. */
 int lb_batch_add(lb_batch *b, int nx, int ny, int nz, double tau, const double *u_lid,

@@ -63,7 +63,7 @@ SIGNATURES = {
     "lb_set_kernel": (_I, [_P, _I, _I]),
     "lb_autotune": (_I, [_P, _I, _P, _P, _P]),
     "lb_totals_static": (_I, [_P, _I64, _P, _I, _I, _I, _I, _P, _P, _P, _P]),
-    "lb_batch_slot_bytes": (_S, [_I, _I, _I, _I]),
+    "lb_batch_slot_bytes": (_S, [_I, _I, _I, _I, _I]),
     "lb_batch_fixed_bytes": (_S, [_I]),
     "lb_batch_create": (_I, [_P, _S, _I, _P]),
     "lb_batch_create_in": (_I, [_P, _P, _S, _I, _P]),

@@ -19,8 +19,8 @@ def _dptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def slot_bytes(nx, ny, nz, storage="f32") -> int:
-    return int(L.lib().lb_batch_slot_bytes(int(nx), int(ny), int(nz), L.STORAGE[storage]))
+def slot_bytes(nx, ny, nz, storage="f32", inplace=False) -> int:
+    return int(L.lib().lb_batch_slot_bytes(int(nx), int(ny), int(nz), L.STORAGE[storage], 1 if inplace else 0))
 
 
 def _bcheck(status: int, what: str):
@@ -80,11 +80,12 @@ class Batch:
 
     # ------------------------------------------------------------------
     def add(self, nx, ny, nz, tau, steps, u_lid=(0.0, 0.0, 0.0), flags=None, storage="f32",
-            force=(0.0, 0.0, 0.0), trt_magic=0.0) -> int:
+            force=(0.0, 0.0, 0.0), trt_magic=0.0, inplace=False) -> int:
         """Admit a lattice; returns its slot.  Raises LbError with status
         LB_ENOMEM (pool full) or LB_EBUSY (no free slot) when it does not fit.
-        trt_magic > 0 selects the two-relaxation-time collision."""
-        opts = make_options(storage, force, trt_magic=trt_magic)
+        trt_magic > 0 selects the two-relaxation-time collision; inplace keeps
+        one population array (half the population memory)."""
+        opts = make_options(storage, force, trt_magic=trt_magic, inplace=inplace)
         ulid = (ctypes.c_double * 3)(*[float(v) for v in u_lid])
         fl = None
         if flags is not None:

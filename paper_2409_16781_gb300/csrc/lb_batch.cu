@@ -26,7 +26,8 @@ namespace lbgb {
 namespace {
 
 constexpr int BATCH_THREADS = 128;   // cells per work item = threads per block
-constexpr int BATCH_TYPES = 5;       // storage types
+constexpr int BATCH_STORAGES = 5;    // storage types
+constexpr int BATCH_TYPES = 10;      // kernel types: storage x (two arrays, in place)
 constexpr int GRAPH_STEPS = 8;       // batched steps per captured graph
 constexpr size_t BALIGN = 256;
 
@@ -55,18 +56,26 @@ __device__ __forceinline__ int fdiv(int n, const FastDiv& f) {
 }
 
 struct SlotDev {
-    void* pop[2];
+    void* pop[2];    // A/B arrays; an in-place slot has one array (pop[0] == pop[1])
     const uint8_t* code;
     LatticeParams p;
     FastDiv div_x;   // nx
     FastDiv div_xy;  // nx * ny
     int storage;
     int force;
+    int inplace;     // parity 0: swapped layout, 1: streamed layout
 };
 
-template <class S, bool FORCE>
+template <class S, bool FORCE, bool INPLACE>
 __device__ __forceinline__ void update_cell(const SlotDev& sd, int parity, int cell, int x, int y, int z, uint8_t cc) {
     using M = typename Storage<S>::math;
+    if constexpr (INPLACE) {  // pop[0] and pop[1] are the one array
+        const S* Ar = static_cast<const S*>(sd.pop[0]);
+        S* Aw = static_cast<S*>(sd.pop[1]);
+        if (parity == 0) inplace_update<S, FORCE, FORM_SWAPPED>(Ar, Aw, sd.code, sd.p, x, y, z, cell, cc);
+        else inplace_update<S, FORCE, FORM_STREAMED>(Ar, Aw, sd.code, sd.p, x, y, z, cell, cc);
+        return;
+    }
     const S* A = static_cast<const S*>(sd.pop[parity]);
     S* B = static_cast<S*>(sd.pop[parity ^ 1]);
     M d[Q];
@@ -76,10 +85,12 @@ __device__ __forceinline__ void update_cell(const SlotDev& sd, int parity, int c
     for (int i = 0; i < Q; ++i) B[(int64_t)i * sd.p.ps + cell] = Storage<S>::store(d[i]);
 }
 
-// One batched step for every active slot of storage type S.
+// One batched step for every active slot of storage type S and one
+// population layout (two arrays, or in place -- separate kernels, so that the
+// two-array kernel keeps its register count).
 //   act[0..n)  slot ids, off[0..n]  cumulative 128-cell item counts,
 //   n = *nact.  Slots whose remaining count is 0 are skipped.
-template <class S>
+template <class S, bool INPLACE>
 __global__ void __launch_bounds__(BATCH_THREADS) batch_step_kernel(const SlotDev* __restrict__ slots,
                                                                    const int* __restrict__ parity,
                                                                    const int64_t* __restrict__ remaining,
@@ -114,9 +125,9 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_step_kernel(const SlotDev
         if (cc & CODE_TYPE) continue;
         const int par = parity[slot];
         if (sd.force)
-            update_cell<S, true>(sd, par, cell, x, y, z, cc);
+            update_cell<S, true, INPLACE>(sd, par, cell, x, y, z, cc);
         else
-            update_cell<S, false>(sd, par, cell, x, y, z, cc);
+            update_cell<S, false, INPLACE>(sd, par, cell, x, y, z, cc);
     }
 }
 
@@ -206,10 +217,19 @@ class Pool {
     size_t size_ = 0;
 };
 
-size_t slot_bytes(int nx, int ny, int nz, int storage) {
+// Kernel type of a slot: its storage, plus BATCH_STORAGES if it is in place.
+inline int kernel_type(int storage, int inplace) { return storage + (inplace ? BATCH_STORAGES : 0); }
+
+size_t slot_bytes(int nx, int ny, int nz, int storage, int inplace) {
     const int64_t N = (int64_t)nx * ny * nz;
     const int64_t ps = (int64_t)rup((size_t)N, 128);
-    return 2 * rup((size_t)Q * ps * storage_bytes(storage), BALIGN) + rup((size_t)N, BALIGN);
+    return (inplace ? 1 : 2) * rup((size_t)Q * ps * storage_bytes(storage), BALIGN) + rup((size_t)N, BALIGN);
+}
+
+// Layout of a slot's state for the readers: the parity of an in-place slot
+// names its layout; a two-array slot's current array is pop[parity].
+inline int slot_form(const SlotDev& d, int par) {
+    return d.inplace ? (par ? FORM_STREAMED : FORM_SWAPPED) : FORM_AB;
 }
 
 struct SlotHost {
@@ -287,7 +307,8 @@ struct lb_batch {
     cudaEvent_t up_ev[NUP] = {};
     int up_next = 0;
     bool dirty = true;
-    int grid[BATCH_TYPES] = {0, 0, 0, 0, 0};
+    int grid[BATCH_TYPES] = {};
+    unsigned types_used = 0;  // kernel types that have had a slot: the ones a step launches
     cudaGraphExec_t graph = nullptr;
 };
 
@@ -393,7 +414,7 @@ int rebuild_lists(lb_batch* b) {
     for (int s = 0; s < M; ++s) {
         const SlotHost& h = b->slots[s];
         if (!h.used) continue;
-        const int t = h.storage;
+        const int t = kernel_type(h.storage, h.dev.inplace);
         const int64_t items = (h.dev.p.N + BATCH_THREADS - 1) / BATCH_THREADS;
         int* o = offs + (size_t)t * (M + 1);
         if ((int64_t)o[counts[t]] + items >= (int64_t(1) << 31)) return bfail(LB_ENOMEM, "batch: too many cells");
@@ -422,38 +443,39 @@ int rebuild_lists(lb_batch* b) {
     return LB_OK;
 }
 
+template <class S, bool INPLACE>
+static void launch_typed(lb_batch* b, int t, cudaStream_t st) {
+    batch_step_kernel<S, INPLACE><<<b->grid[t], BATCH_THREADS, 0, st>>>(b->d_slots, b->d_parity, b->d_remaining,
+                                                                         b->d_act[t], b->d_off[t], b->d_nact + t);
+}
+
 cudaError_t launch_type(lb_batch* b, int t, cudaStream_t st) {
-    const int grid = b->grid[t];
     switch (t) {
-        case 0:
-            batch_step_kernel<double><<<grid, BATCH_THREADS, 0, st>>>(b->d_slots, b->d_parity, b->d_remaining,
-                                                                      b->d_act[0], b->d_off[0], b->d_nact + 0);
-            break;
-        case 1:
-            batch_step_kernel<float><<<grid, BATCH_THREADS, 0, st>>>(b->d_slots, b->d_parity, b->d_remaining,
-                                                                     b->d_act[1], b->d_off[1], b->d_nact + 1);
-            break;
-        case 2:
-            batch_step_kernel<__half><<<grid, BATCH_THREADS, 0, st>>>(b->d_slots, b->d_parity, b->d_remaining,
-                                                                      b->d_act[2], b->d_off[2], b->d_nact + 2);
-            break;
-        case 3:
-            batch_step_kernel<__nv_bfloat16><<<grid, BATCH_THREADS, 0, st>>>(
-                b->d_slots, b->d_parity, b->d_remaining, b->d_act[3], b->d_off[3], b->d_nact + 3);
-            break;
-        default:
-            batch_step_kernel<f32d><<<grid, BATCH_THREADS, 0, st>>>(b->d_slots, b->d_parity, b->d_remaining,
-                                                                    b->d_act[4], b->d_off[4], b->d_nact + 4);
-            break;
+        case 0: launch_typed<double, false>(b, t, st); break;
+        case 1: launch_typed<float, false>(b, t, st); break;
+        case 2: launch_typed<__half, false>(b, t, st); break;
+        case 3: launch_typed<__nv_bfloat16, false>(b, t, st); break;
+        case 4: launch_typed<f32d, false>(b, t, st); break;
+        case 5: launch_typed<double, true>(b, t, st); break;
+        case 6: launch_typed<float, true>(b, t, st); break;
+        case 7: launch_typed<__half, true>(b, t, st); break;
+        case 8: launch_typed<__nv_bfloat16, true>(b, t, st); break;
+        default: launch_typed<f32d, true>(b, t, st); break;
     }
     return cudaGetLastError();
 }
 
-// One batched step: the four storage-type kernels run concurrently on side
+template <class S, bool INPLACE>
+static cudaError_t occupancy_of(int* per) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, batch_step_kernel<S, INPLACE>, BATCH_THREADS, 0);
+}
+
+// One batched step: the kernels of the types in use run concurrently on side
 // streams forked from the batch stream, then the advance kernel.
 cudaError_t issue_step(lb_batch* b) {
     cudaError_t e = cudaEventRecord(b->fork, b->stream);
     for (int t = 0; t < BATCH_TYPES && e == cudaSuccess; ++t) {
+        if (!((b->types_used >> t) & 1u)) continue;
         e = cudaStreamWaitEvent(b->side[t], b->fork, 0);
         if (e == cudaSuccess) e = launch_type(b, t, b->side[t]);
         if (e == cudaSuccess) e = cudaEventRecord(b->join[t], b->side[t]);
@@ -607,17 +629,17 @@ int batch_create_common(lb_batch** out, size_t capacity, int max_slots, void* st
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) {
-        int per[BATCH_TYPES] = {0, 0, 0, 0, 0};
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], batch_step_kernel<double>, BATCH_THREADS, 0);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], batch_step_kernel<float>, BATCH_THREADS, 0);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[2], batch_step_kernel<__half>, BATCH_THREADS, 0);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[3], batch_step_kernel<__nv_bfloat16>, BATCH_THREADS,
-                                                              0);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[4], batch_step_kernel<f32d>, BATCH_THREADS, 0);
+        int per[BATCH_TYPES] = {};
+        e = occupancy_of<double, false>(&per[0]);
+        if (e == cudaSuccess) e = occupancy_of<float, false>(&per[1]);
+        if (e == cudaSuccess) e = occupancy_of<__half, false>(&per[2]);
+        if (e == cudaSuccess) e = occupancy_of<__nv_bfloat16, false>(&per[3]);
+        if (e == cudaSuccess) e = occupancy_of<f32d, false>(&per[4]);
+        if (e == cudaSuccess) e = occupancy_of<double, true>(&per[5]);
+        if (e == cudaSuccess) e = occupancy_of<float, true>(&per[6]);
+        if (e == cudaSuccess) e = occupancy_of<__half, true>(&per[7]);
+        if (e == cudaSuccess) e = occupancy_of<__nv_bfloat16, true>(&per[8]);
+        if (e == cudaSuccess) e = occupancy_of<f32d, true>(&per[9]);
         for (int t = 0; t < BATCH_TYPES; ++t) b->grid[t] = sms * (per[t] > 0 ? per[t] : 1);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -654,10 +676,10 @@ int reader_for(lb_batch* b, int slot, cudaStream_t* st, double** staging, int* p
 
 extern "C" {
 
-size_t lb_batch_slot_bytes(int nx, int ny, int nz, int storage) {
+size_t lb_batch_slot_bytes(int nx, int ny, int nz, int storage, int inplace) {
     if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz >= (int64_t(1) << 31)) return 0;
-    if (storage < LB_F64 || storage > LB_F32D) return 0;
-    return slot_bytes(nx, ny, nz, storage);
+    if (storage < LB_F64 || storage > LB_F32D || (inplace != 0 && inplace != 1)) return 0;
+    return slot_bytes(nx, ny, nz, storage, inplace);
 }
 
 size_t lb_batch_fixed_bytes(int max_slots) {
@@ -687,6 +709,7 @@ int lb_batch_add(lb_batch* b, int nx, int ny, int nz, double tau, const double* 
     if (o.storage < LB_F64 || o.storage > LB_F32D) return bfail(LB_EINVAL, "lb_batch_add: bad storage");
     if (!(o.trt_magic >= 0.0) || !std::isfinite(o.trt_magic))
         return bfail(LB_EINVAL, "lb_batch_add: trt_magic must be >= 0");
+    if (o.inplace != 0 && o.inplace != 1) return bfail(LB_EINVAL, "lb_batch_add: inplace must be 0 or 1");
     if (steps < 0) return bfail(LB_EINVAL, "lb_batch_add: steps < 0");
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(o.force[a]) || (u_lid && !std::isfinite(u_lid[a])))
@@ -702,7 +725,7 @@ int lb_batch_add(lb_batch* b, int nx, int ny, int nz, double tau, const double* 
             break;
         }
     if (slot < 0) return bfail(LB_EBUSY, "lb_batch_add: all %d slots in use", b->max_slots);
-    const size_t need = slot_bytes(nx, ny, nz, o.storage);
+    const size_t need = slot_bytes(nx, ny, nz, o.storage, o.inplace);
     size_t off = 0;
     if (!b->pool.alloc(need, &off))
         return bfail(LB_ENOMEM, "lb_batch_add: %zu bytes do not fit the pool (%zu free)", need, b->pool.free_bytes());
@@ -712,8 +735,9 @@ int lb_batch_add(lb_batch* b, int nx, int ny, int nz, double tau, const double* 
     char* base = b->pool_base + off;
     SlotDev d;
     d.pop[0] = base;
-    d.pop[1] = base + popb;
-    d.code = (const uint8_t*)(base + 2 * popb);
+    d.pop[1] = o.inplace ? base : base + popb;
+    d.code = (const uint8_t*)(base + (o.inplace ? 1 : 2) * popb);
+    d.inplace = o.inplace;
     d.p.nx = nx;
     d.p.ny = ny;
     d.p.nz = nz;
@@ -740,7 +764,8 @@ int lb_batch_add(lb_batch* b, int nx, int ny, int nz, double tau, const double* 
     } else {
         e = cudaMemsetAsync(code, 0, (size_t)N, b->io);
     }
-    if (e == cudaSuccess) e = launch_init(o.storage, d.pop[0], d.pop[1], ps, nullptr, nullptr, 0, 0, N, b->io);
+    if (e == cudaSuccess)
+        e = launch_init(o.storage, d.pop[0], d.pop[1], ps, nullptr, nullptr, 0, 0, N, b->io, o.inplace);
     if (e == cudaSuccess) e = cudaEventRecord(b->io_ev, b->io);
     // descriptor and counters on the main stream, after the set-up
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->io_ev, 0);
@@ -766,6 +791,19 @@ int lb_batch_add(lb_batch* b, int nx, int ny, int nz, double tau, const double* 
     if (e != cudaSuccess) {
         b->pool.release(off, need);
         return bcuda(e, "lb_batch_add");
+    }
+    const unsigned tbit = 1u << kernel_type(o.storage, o.inplace);
+    if (!(b->types_used & tbit)) {
+        // a kernel type not launched so far: the captured step graph lacks its
+        // kernel, so it is re-captured at the next lb_batch_step (after the
+        // replays already queued have finished)
+        if (b->graph) {
+            cudaError_t eg = cudaStreamSynchronize(b->stream);
+            if (eg == cudaSuccess) eg = cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+            if (eg != cudaSuccess) return bcuda(eg, "lb_batch_add: graph");
+        }
+        b->types_used |= tbit;
     }
     h.used = true;
     h.storage = o.storage;
@@ -852,9 +890,18 @@ int lb_batch_init_fields(lb_batch* b, int slot, const double* rho, const double*
         for (int a = 0; a < 3 && u && e == cudaSuccess; ++a)
             e = cudaMemcpyAsync(du + a * cnt, u + a * N + c0, cnt * 8, cudaMemcpyHostToDevice, b->stream);
         if (e == cudaSuccess)
-            e = launch_init(d.storage, d.pop[par], d.pop[par ^ 1], d.p.ps, drho, du, cnt, c0, cnt, b->stream);
+            e = launch_init(d.storage, d.pop[par], d.pop[par ^ 1], d.p.ps, drho, du, cnt, c0, cnt, b->stream,
+                            d.inplace);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
         if (e != cudaSuccess) return bcuda(e, "lb_batch_init_fields");
+    }
+    if (d.inplace && par != 0) {  // the initialised state has the swapped layout: parity 0
+        const int zero = 0;
+        cudaError_t e = cudaMemcpyAsync(b->d_parity + slot, &zero, sizeof zero, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return bcuda(e, "lb_batch_init_fields: parity");
+        b->last_par[slot] = 0;
+        b->added_seq[slot] = b->snap_head;  // snapshots taken from now on describe it
     }
     return LB_OK;
 }
@@ -954,7 +1001,8 @@ int lb_batch_moments(lb_batch* b, int slot, double* rho, double* u) {
     const int64_t chunk = bchunk(b, 32);
     for (int64_t c0 = 0; c0 < N; c0 += chunk) {
         const int64_t cnt = (N - c0 < chunk) ? N - c0 : chunk;
-        cudaError_t e = launch_moments(d.storage, d.pop[par], d.code, d.p, stg, stg + cnt, cnt, c0, cnt, st);
+        cudaError_t e =
+            launch_moments(d.storage, d.pop[par], d.code, d.p, stg, stg + cnt, cnt, c0, cnt, st, slot_form(d, par));
         if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho + c0, stg, cnt * 8, cudaMemcpyDeviceToHost, st);
         for (int a = 0; a < 3 && u && e == cudaSuccess; ++a)
             e = cudaMemcpyAsync(u + a * N + c0, stg + (1 + a) * cnt, cnt * 8, cudaMemcpyDeviceToHost, st);
@@ -973,7 +1021,7 @@ int lb_batch_totals(lb_batch* b, int slot, double* mass, double* mom) {
     if ((rc = reader_for(b, slot, &st, &stg, &par)) != LB_OK) return rc;
     const SlotDev& d = b->slots[slot].dev;
     double out[5];
-    cudaError_t e = launch_totals(d.storage, d.pop[par], d.code, d.p, b->partials, b->tot_out, st);
+    cudaError_t e = launch_totals(d.storage, d.pop[par], d.code, d.p, b->partials, b->tot_out, st, slot_form(d, par));
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, b->tot_out, sizeof out, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return bcuda(e, "lb_batch_totals");
@@ -998,7 +1046,7 @@ int lb_batch_get_populations(lb_batch* b, int slot, double* f) {
     const int64_t chunk = bchunk(b, Q * 8);
     for (int64_t c0 = 0; c0 < N; c0 += chunk) {
         const int64_t cnt = (N - c0 < chunk) ? N - c0 : chunk;
-        cudaError_t e = launch_get_pops(d.storage, d.pop[par], d.code, d.p, FORM_AB, c0, cnt, stg, st);
+        cudaError_t e = launch_get_pops(d.storage, d.pop[par], d.code, d.p, slot_form(d, par), c0, cnt, stg, st);
         for (int i = 0; i < Q && e == cudaSuccess; ++i)
             e = cudaMemcpyAsync(f + i * N + c0, stg + i * cnt, cnt * 8, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1018,14 +1066,30 @@ int lb_batch_fetch(lb_batch* b, int slot, double* rho, double* u) {
     const SlotDev& d = b->slots[slot].dev;
     const int par = b->last_par[slot];
     const int64_t N = d.p.N;
-    // the finished slot's B array (>= 38 bytes per cell) holds rho and u
-    double* dr = (double*)d.pop[par ^ 1];
-    double* du = dr + N;
     cudaError_t e = cudaSuccess;
     if (!b->fetch_ev[slot]) e = cudaEventCreateWithFlags(&b->fetch_ev[slot], cudaEventDisableTiming);
-    if (e == cudaSuccess) e = launch_moments(d.storage, d.pop[par], d.code, d.p, dr, du, N, 0, N, b->io);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(rho, dr, (size_t)N * 8, cudaMemcpyDeviceToHost, b->io);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(u, du, (size_t)N * 24, cudaMemcpyDeviceToHost, b->io);
+    if (!d.inplace) {
+        // the finished slot's B array (>= 38 bytes per cell) holds rho and u
+        double* dr = (double*)d.pop[par ^ 1];
+        double* du = dr + N;
+        if (e == cudaSuccess) e = launch_moments(d.storage, d.pop[par], d.code, d.p, dr, du, N, 0, N, b->io);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(rho, dr, (size_t)N * 8, cudaMemcpyDeviceToHost, b->io);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(u, du, (size_t)N * 24, cudaMemcpyDeviceToHost, b->io);
+    } else {
+        // no spare array: chunks through the io staging area, each chunk's
+        // moments kernel ordered after the previous chunk's copies on the
+        // io stream (so the host never waits here)
+        const int64_t chunk = bchunk(b, 32);
+        double* stg = (double*)b->io_staging;
+        for (int64_t c0 = 0; c0 < N && e == cudaSuccess; c0 += chunk) {
+            const int64_t cnt = (N - c0 < chunk) ? N - c0 : chunk;
+            e = launch_moments(d.storage, d.pop[par], d.code, d.p, stg, stg + cnt, cnt, c0, cnt, b->io,
+                               slot_form(d, par));
+            if (e == cudaSuccess) e = cudaMemcpyAsync(rho + c0, stg, cnt * 8, cudaMemcpyDeviceToHost, b->io);
+            for (int a = 0; a < 3 && e == cudaSuccess; ++a)
+                e = cudaMemcpyAsync(u + a * N + c0, stg + (1 + a) * cnt, cnt * 8, cudaMemcpyDeviceToHost, b->io);
+        }
+    }
     if (e == cudaSuccess) e = cudaEventRecord(b->fetch_ev[slot], b->io);
     if (e != cudaSuccess) return bcuda(e, "lb_batch_fetch");
     b->fetching[slot] = 1;

@@ -28,36 +28,16 @@ namespace lbgb {
 template <class S, bool FORCE, int FORM>
 __global__ void __launch_bounds__(512) step_kernel_inplace(const S* Ar, S* Aw, const uint8_t* __restrict__ code,
                                                            LatticeParams p, int xblocks) {
-    using M = typename Storage<S>::math;
     const int xb = blockIdx.x % xblocks;
     const int row = blockIdx.x / xblocks;
     const int x = xb * blockDim.x + threadIdx.x;
     if (x >= p.nx) return;
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int y = row % ny;
-    const int z = row / ny;
-    const int cell = x + nx * row;
+    const int y = row % p.ny;
+    const int z = row / p.ny;
+    const int cell = x + p.nx * row;
     const uint8_t cc = code[cell];
     if (cc & CODE_TYPE) return;  // solid cells hold no values of their own
-    M d[Q];
-    pull_cell<S, 0, FORM>(Ar, code, p, x, y, z, cell, cc, d);
-    relax_dev<M, FORCE>(d, p);
-    if constexpr (FORM == FORM_STREAMED) {
-        // -> FORM_SWAPPED: P_i(x) into plane opp(i) at x
-#pragma unroll
-        for (int i = 0; i < Q; ++i) Aw[(int64_t)D3Q19::opp(i) * p.ps + cell] = Storage<S>::store(d[i]);
-    } else {
-        // -> FORM_STREAMED: P_i(x) into plane i at x + c_i (periodic wrap)
-        const int nxy = nx * ny;
-        const int xt[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
-        const int yt[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
-        const int zt[3] = {(z == 0 ? nz - 1 : z - 1) * nxy, z * nxy, (z == nz - 1 ? 0 : z + 1) * nxy};
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            const int t = xt[D3Q19::cx(i) + 1] + yt[D3Q19::cy(i) + 1] + zt[D3Q19::cz(i) + 1];
-            Aw[(int64_t)i * p.ps + t] = Storage<S>::store(d[i]);
-        }
-    }
+    inplace_update<S, FORCE, FORM>(Ar, Aw, code, p, x, y, z, cell, cc);
 }
 
 template <class S, int FORM>

@@ -376,4 +376,33 @@ __device__ __forceinline__ void relax_dev(M (&d)[Q], const LatticeParams& p) {
     for (int i = 0; i < Q; ++i) d[i] = out[i];
 }
 
+// One in-place ("AA") update of fluid cell (x, y, z) whose state has layout
+// FORM (FORM_SWAPPED or FORM_STREAMED): pull, collide, and store in the other
+// layout -- from FORM_STREAMED into plane opp(i) at the cell, from
+// FORM_SWAPPED into plane i at x + c_i (periodic wrap).  Ar and Aw are the
+// same array (see step_kernel_inplace for why they are two pointers).
+template <class S, bool FORCE, int FORM>
+__device__ __forceinline__ void inplace_update(const S* Ar, S* Aw, const uint8_t* __restrict__ code,
+                                               const LatticeParams& p, int x, int y, int z, int cell, uint8_t cc) {
+    using M = typename Storage<S>::math;
+    M d[Q];
+    pull_cell<S, 0, FORM>(Ar, code, p, x, y, z, cell, cc, d);
+    relax_dev<M, FORCE>(d, p);
+    if constexpr (FORM == FORM_STREAMED) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Aw[(int64_t)D3Q19::opp(i) * p.ps + cell] = Storage<S>::store(d[i]);
+    } else {
+        const int nx = p.nx, ny = p.ny, nz = p.nz;
+        const int nxy = nx * ny;
+        const int xt[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+        const int yt[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
+        const int zt[3] = {(z == 0 ? nz - 1 : z - 1) * nxy, z * nxy, (z == nz - 1 ? 0 : z + 1) * nxy};
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int t = xt[D3Q19::cx(i) + 1] + yt[D3Q19::cy(i) + 1] + zt[D3Q19::cz(i) + 1];
+            Aw[(int64_t)i * p.ps + t] = Storage<S>::store(d[i]);
+        }
+    }
+}
+
 }  // namespace lbgb

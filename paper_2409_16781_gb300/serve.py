@@ -244,15 +244,18 @@ class BatchBackend:
     """The serving form: every admitted request is a slot of one lb_batch;
     results come back asynchronously (lb_batch_fetch) into pinned buffers."""
 
-    def __init__(self, capacity_bytes: int, max_slots: int = 1024, device=None, keep_fields: bool = False):
+    def __init__(self, capacity_bytes: int, max_slots: int = 1024, device=None, keep_fields: bool = False,
+                 inplace: bool = False):
         from .batch import Batch
         self.batch = Batch(capacity_bytes, max_slots=max_slots, device=device)
         self.keep = keep_fields
+        self.inplace = inplace  # one population array per slot: about twice the requests per budget
         self.pending = {}
 
     def admit(self, req):
         return self.batch.try_add(req.nx, req.ny, req.nz, req.tau, req.steps, u_lid=req.u_lid,
-                                  flags=req.flags(), storage=req.storage, force=req.force)
+                                  flags=req.flags(), storage=req.storage, force=req.force,
+                                  inplace=self.inplace)
 
     def step(self, n):
         self.batch.step(n)

@@ -212,3 +212,87 @@ def test_step_quotas():
     _, ua = a7.moments()
     assert vel_err(u0, ua, W.cavity_flags(12, 10, 8) == 0) <= 1e-5
     b.close()
+
+
+def test_inplace_slots_in_the_mix():
+    """In-place slots (one population array each) next to two-array slots of
+    every storage: each gives the same result as the lattice alone (bitwise
+    for the fluid cells: same pull, same collision), after odd and even
+    step counts; fetch reads them back through the staging area."""
+    b = Batch(capacity_bytes=64 << 20, max_slots=16)
+    slots = []
+    for k, (nx, ny, nz, tau, storage, kind, steps) in enumerate(MIX):
+        flags, ulid, g = _geom(nx, ny, nz, kind)
+        slots.append(b.add(nx, ny, nz, tau, steps, u_lid=ulid, flags=flags, storage=storage, force=g,
+                           inplace=(k % 2 == 0)))
+    b.step(60)
+    assert set(b.poll()) == set(slots)
+    for k, (s, (nx, ny, nz, tau, storage, kind, steps)) in enumerate(zip(slots, MIX)):
+        flags, ulid, g = _geom(nx, ny, nz, kind)
+        alone = Lattice(nx, ny, nz, tau, u_lid=ulid, flags=flags, storage=storage, force=g, kernel=1)
+        alone.step(steps)
+        mask = fluid_mask(flags, alone.shape)
+        fb, fa = b.populations(s), alone.populations()
+        assert np.array_equal(fb[:, mask], fa[:, mask]), (k, storage)
+        rb, ub = b.moments(s)
+        ra, ua = alone.moments()
+        assert np.array_equal(ub, ua) and np.array_equal(rb, ra)
+        mb, pb = b.totals(s)
+        ma, pa = alone.totals()
+        assert mb == ma and np.array_equal(pb, pa)
+        # asynchronous read-back (the in-place slots through the staging area)
+        rho = np.empty((nz, ny, nx))
+        u = np.empty((3, nz, ny, nx))
+        b.fetch(s, rho, u)
+        while not b.fetch_done(s):
+            pass
+        assert np.array_equal(rho, ra) and np.array_equal(u, ua)
+        alone.close()
+    b.close()
+
+
+def test_inplace_admission_and_init_fields():
+    """A pool that holds two two-array FP32 slots holds three in-place ones;
+    re-initialising an in-place slot after an odd number of steps resets its
+    layout; adding the first in-place slot after graph replays re-captures
+    the step graph."""
+    two = slot_bytes(16, 16, 16, "f32")
+    one = slot_bytes(16, 16, 16, "f32", inplace=True)
+    assert two - one == 19 * 16 ** 3 * 4
+    b = Batch(capacity_bytes=2 * two, max_slots=4)
+    s0 = b.add(16, 16, 16, 0.7, 100)
+    b.step(16)  # graph path with the two-array kernel only
+    b.remove(s0)
+    ss = [b.add(16, 16, 16, 0.7, 100, inplace=True) for _ in range(3)]
+    assert b.try_add(16, 16, 16, 0.7, 10, inplace=True) is None
+    rho0, u0 = W.random_fields(16, 16, 16, seed=2, du=0.04, drho=0.01)
+    b.step(17)                     # odd: streamed layout
+    b.init_fields(ss[1], rho0, u0)  # back to the swapped layout
+    b.step(24)                     # graph re-captured with the in-place kernel
+    alone = Lattice(16, 16, 16, 0.7, storage="f32", kernel=1)
+    alone.step(41)
+    ref = Lattice(16, 16, 16, 0.7, storage="f32", kernel=1)
+    ref.init_fields(rho0, u0)
+    ref.step(24)
+    for s in ss:
+        f = b.populations(s)
+        want = ref.populations() if s == ss[1] else alone.populations()
+        assert np.array_equal(f, want)
+    b.close()
+
+
+def test_serve_inplace_same_as_sequential():
+    """The batched server with in-place slots gives the same velocity fields
+    as the one-at-a-time baseline."""
+    reqs = W.request_stream(n=8, rate_hz=200.0, seed=9, min_cells=6 ** 3, max_cells=20 ** 3,
+                            steps_range=(20, 120))
+    be = BatchBackend(capacity_bytes=64 << 20, max_slots=8, keep_fields=True, inplace=True)
+    st = serve(reqs, be, chunk_ms=2.0, policy="srpt", target_cells=5000)
+    be.close()
+    assert len(st.results) == len(reqs) and not st.rejected
+    got = {r.rid: r.checksum for r in st.results}
+    for req in reqs:
+        st1 = serve([req], SequentialBackend(storage=req.storage, keep_fields=True))
+        ref = st1.results[0].checksum
+        tol = 1e-5 if req.storage == "f32" else 2e-3
+        assert abs(got[req.rid] - ref) <= tol * max(ref, 1e-12) + 1e-12
