@@ -68,9 +68,12 @@ def parse_args(argv=None):
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use the library default variant instead of the autotuner's choice")
-    ap.add_argument("--workload", choices=["tgv", "serve", "porous", "precision"], default="tgv",
+    ap.add_argument("--workload", choices=["tgv", "serve", "porous", "precision", "vks"], default="tgv",
                     help="tgv: the 256^3 Taylor-Green line (default); serve: a full serving run; "
-                         "porous: the 512^3 porous channel; precision: the 768^3 cavity precision study")
+                         "porous: the 512^3 porous channel; precision: the 768^3 cavity precision study; "
+                         "vks: flow past a cylinder (von Karman street), 1024x256x64")
+    ap.add_argument("--vks-steps", type=int, default=40000,
+                    help="steps of the von Karman street run that measures the shedding frequency")
     ap.add_argument("--taus", default="0.52,0.56,0.6", help="relaxation times of the precision study")
     ap.add_argument("--serve-requests", type=int, default=80,
                     help="requests in the serving section of the default line (0 = skip)")
@@ -545,8 +548,9 @@ def main(argv=None):
         return 0
     dist = Dist()
     try:
-        if args.workload in ("serve", "porous", "precision"):
-            fn = {"serve": serve_line, "porous": porous_line, "precision": precision_line}[args.workload]
+        if args.workload in ("serve", "porous", "precision", "vks"):
+            fn = {"serve": serve_line, "porous": porous_line, "precision": precision_line,
+                  "vks": vks_line}[args.workload]
             if dist.rank == 0:
                 print(json.dumps(fn(args)), flush=True)
             return 0
@@ -608,6 +612,92 @@ def porous_line(args):
             "roofline": {"bound": "hbm", "achieved": round(bpu * N / (sec / K) / 1e9, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(bpu * N / (sec / K) / 1e9 / peak, 4), "peak_kind": kind},
             "mass_drift_rel": abs(m1 - m0) / m0, "momentum_x": p1[0]}
+
+
+def vks_line(args):
+    """Flow past a cylinder, the paper's von Karman street use case in 3D:
+    1024 x 256 x 64 cells, a cylinder along z of diameter D = 32 at x = 8D,
+    far-field (free stream) planes at x = 0 and x = nx-1, periodic y and z,
+    free stream U = 0.05 along x, Re = U D / nu = 100.  Throughput: CUDA
+    events around 2000 steps (autotuned kernel); then a longer run started
+    from the free stream with a small asymmetric kick measures the shedding
+    frequency from u_y one diameter pair behind the cylinder (Strouhal
+    number St = f D / U; about 0.16-0.19 expected at Re 100 for an
+    unconfined to 1/8-blocked cylinder -- a check of the physics, not a
+    parity pin)."""
+    import numpy as np
+    import torch
+
+    from paper_2409_16781_gb300 import Lattice, velocity_set
+    from paper_2409_16781_gb300 import workloads as W
+    nx, ny, nz, D, U, Re = 1024, 256, 64, 32, 0.05, 100.0
+    tau = 0.5 + 3.0 * U * D / Re
+    cx, cy = 8 * D, ny / 2 + 0.5
+    flags = W.cylinder_flags(nx, ny, nz, diameter=D, cx=cx, cy=cy)
+    N = nx * ny * nz
+    fluid = int((flags == 0).sum())
+    stream = torch.cuda.current_stream()
+    lat = Lattice(nx, ny, nz, tau, u_lid=(U, 0.0, 0.0), flags=flags, storage=args.storage, stream=stream,
+                  trt_magic=args.trt_magic, inplace=args.inplace)
+    u0 = np.zeros((3, nz, ny, nx))
+    u0[0] = U
+    u0[0][flags != 0] = 0.0
+    # an asymmetric kick behind the cylinder so that shedding starts early
+    kick = np.zeros((nz, ny, nx), bool)
+    kick[:, int(cy):int(cy) + D, int(cx) + D // 2:int(cx) + 3 * D] = True
+    u0[1][kick & (flags == 0)] = 0.2 * U
+    lat.init_fields(None, u0)
+    v, b, _ = lat.autotune(reps=10, cache=False)
+    lat.step(20)
+    K = 2000
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.step(K)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    mlups = N / ms / 1e3
+    # shedding frequency
+    lat.init_fields(None, u0)
+    c, _ = velocity_set()
+    probe = np.array([int(cx + 2 * D) + nx * (int(cy) + ny * (nz // 2))])
+    every, uy = 25, []
+    for _ in range(args.vks_steps // every):
+        lat.step(every)
+        f = lat.populations_at(probe)[0]
+        uy.append(float(f @ c[:, 1]) / float(f.sum()))
+    uy = np.array(uy)
+    # the period from the zero crossings (linear interpolation) of u_y over
+    # the second half of the run, once the street is established
+    tail = uy[len(uy) // 2:] - uy[len(uy) // 2:].mean()
+    t = (np.arange(len(tail)) + len(uy) - len(tail)) * every
+    up = np.nonzero((tail[:-1] < 0) & (tail[1:] >= 0))[0]
+    tc = t[up] + every * (-tail[up]) / (tail[up + 1] - tail[up])
+    st = float(D / (U * np.diff(tc).mean())) if len(tc) >= 2 else None
+    m, _ = lat.totals()
+    lat.close()
+    peak, peak_kind = measured_peaks()
+    gbs = mlups * 1e6 * bytes_per_update(args.storage) / 1e9
+    return {
+        "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": 1, "steps": K, "warmup": 20,
+        "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": args.storage, "data": "synthetic",
+        "config": {"workload": f"von Karman street (flow past a cylinder) {nx}x{ny}x{nz}, D={D}, "
+                               f"U={U}, Re={Re:g}, tau={tau:.4f}, {args.storage} populations, far-field "
+                               "inflow/outflow planes, periodic y and z",
+                   "kernel": {"variant": v, "block": b}, "inplace": bool(args.inplace),
+                   "collision": f"TRT {args.trt_magic}" if args.trt_magic else "BGK"},
+        "fluid_mlups": round(mlups * fluid / N, 1),
+        "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(gbs / peak, 4), "peak_kind": peak_kind, "traffic": None},
+        "shedding": {"strouhal": None if st is None else round(st, 4), "periods_seen": int(max(len(tc) - 1, 0)),
+                     "probe": "u_y at (x0 + 2D, y0, nz/2)",
+                     "samples": len(uy), "every_steps": every, "steps": args.vks_steps,
+                     "uy_amplitude_over_U": round(float(np.abs(tail).max()) / U, 4)},
+        "mass_per_fluid_cell": m / fluid,
+        "gpu_launches": K,
+    }
 
 
 def precision_line(args):

@@ -21,7 +21,7 @@
  *    column-major order of Sec. 4.2).  A vector field u is SoA: u[a*N + cell],
  *    a = 0,1,2 for x,y,z.  Populations are q-major: f[i*N + cell].
  *  - The domain wraps periodically on all six faces; walls are cells
- *    flagged LB_WALL or LB_LID.
+ *    flagged LB_WALL or LB_LID, open boundaries cells flagged LB_FARFIELD.
  *  - Velocity order (fixed): i = 0 rest; 1..6 = +x,-x,+y,-y,+z,-z;
  *    7..18 = (1,1,0),(-1,-1,0),(1,-1,0),(-1,1,0),(1,0,1),(-1,0,-1),
  *    (1,0,-1),(-1,0,1),(0,1,1),(0,-1,-1),(0,1,-1),(0,-1,1).  Directions
@@ -64,8 +64,15 @@ typedef enum {
     LB_F32D = 4   /* "Mixed2": FP32 storage of f - w, FP64 math   */
 } lb_storage;
 
-/* Cell flags (uint8 per cell). */
-enum { LB_FLUID = 0, LB_WALL = 1, LB_LID = 2 };
+/* Cell flags (uint8 per cell).  LB_WALL: no-slip wall (halfway
+ * bounce-back).  LB_LID: wall moving at u_lid (Sec. 3.3, lid-driven cavity).
+ * LB_FARFIELD: the free stream -- a fluid cell pulling from it receives the
+ * equilibrium f^eq(rho = 1, u = u_lid) of Eq. 2-3 whatever it sent out;
+ * planes of far-field cells are the inflow and outflow of flow past an
+ * obstacle (the von Karman street use case of Sec. 3.3, whose boundary
+ * conditions the paper does not give).  Solid and far-field cells are
+ * never updated and report rho = 0, u = 0. */
+enum { LB_FLUID = 0, LB_WALL = 1, LB_LID = 2, LB_FARFIELD = 3 };
 
 typedef struct lb_options {
     int storage;       /* lb_storage; default LB_F32 */
@@ -111,10 +118,11 @@ size_t lb_bytes_required(int nx, int ny, int nz, const lb_options *opt);
 /* Create a lattice (Sec. 3.3 use cases; lb_create(nx,ny,nz,tau,u_lid,flags)
  * of the problem statement).
  *   tau    BGK relaxation time, omega = 1/tau of Eq. 1; must be > 1/2.
- *   u_lid  velocity of LB_LID cells (NULL = 0); halfway bounce-back off a
- *          LID source adds 6 w_i (c_i . u_lid) (wall density 1).
- *   flags  host, N bytes, values LB_FLUID/LB_WALL/LB_LID, copied at create;
- *          NULL = all fluid.
+ *   u_lid  velocity of LB_LID cells and of the free stream of LB_FARFIELD
+ *          cells (NULL = 0); halfway bounce-back off a LID source adds
+ *          6 w_i (c_i . u_lid) (wall density 1).
+ *   flags  host, N bytes, values LB_FLUID/LB_WALL/LB_LID/LB_FARFIELD,
+ *          copied at create; NULL = all fluid.
  *   opt    NULL = defaults.
  * The library allocates lb_bytes_required() bytes of device memory with
  * cudaMalloc; the populations start at rest, f = w (rho = 1, u = 0).
@@ -198,8 +206,8 @@ int lb_autotune(lb_lattice *h, int reps, int *variant, int *block, float *ms_per
  *   populations  device, 19 planes of plane_stride >= N elements of the
  *                storage type, each value the deviation f_i - w_i, library
  *                velocity order (the layout lb_create uses);
- *   flags        device, N bytes, LB_FLUID/LB_WALL/LB_LID (the two low bits
- *                are read);
+ *   flags        device, N bytes, LB_FLUID/LB_WALL/LB_LID/LB_FARFIELD (the
+ *                two low bits are read);
  *   force, u_lid host, 3 doubles each or NULL (= 0);
  *   stream       cudaStream_t or NULL; the call synchronises it;
  *   out          host, 5 doubles: mass, momentum x/y/z, count of fluid

@@ -35,7 +35,7 @@ _lock = threading.Lock()
 _lib = None
 
 Q = 19
-FLUID, WALL, LID = 0, 1, 2
+FLUID, WALL, LID, FARFIELD = 0, 1, 2, 3
 
 
 def compile_source(src: str, out: str) -> str:

@@ -30,7 +30,10 @@
  *     such a cell takes the halfway bounce-back value f_opp(i)*(x), plus
  *     6 w_i rho_w (c_i . u_lid) with rho_w = 1 when the source is a LID cell;
  *   - the pull (Sec. 3.1: "scattered read" from f^pre, result in f^post) wraps
- *     periodically at the domain edges; solid cells are never written.
+ *     periodically at the domain edges; solid cells are never written;
+ *   - von Karman street (Sec. 3.3 names it; no boundary conditions given):
+ *     the inflow and outflow planes are FARFIELD cells held at the free
+ *     stream, the equilibrium of density 1 moving at u_lid (lbo_pull).
  *
  * Array layout used by this file: f[q * N + cell], cell = x + nx*(y + ny*z),
  * q in this file's own velocity order (lbo_velocity_set reports it).
@@ -48,7 +51,9 @@
 
 #define LBO_Q 19
 #define LBO_FLUID 0
+#define LBO_WALL 1
 #define LBO_LID 2
+#define LBO_FARFIELD 3
 
 static int lbo_c[LBO_Q][3];
 static double lbo_w[LBO_Q];
@@ -131,17 +136,29 @@ static inline int lbo_wrap(int v, int n)
 }
 
 /* Streaming (pull) with the boundary rules: the 19 populations arriving at
- * fluid cell (x,y,z) from post-collision array A. */
+ * fluid cell (x,y,z) from post-collision array A.
+ * FARFIELD cells (the inflow and outflow planes of the von Karman street use
+ * case, flow past a cylinder, Sec. 3.3, whose boundary conditions the paper
+ * does not give): the free stream -- the value arriving from a far-field
+ * source is the equilibrium f^eq_i(rho = 1, U) of Eq. 2-3 with U = u_lid,
+ * whatever the fluid sends out (an absorbing, Dirichlet condition on both
+ * density and velocity). */
 static void lbo_pull(int nx, int ny, int nz, const double *ulid, const uint8_t *flags,
                      const double *A, int x, int y, int z, double *f)
 {
     size_t N = (size_t)nx * ny * nz;
     size_t cell = lbo_idx(x, y, z, nx, ny);
+    double f_free[LBO_Q];
+    if (flags != NULL) lbo_equilibrium(1.0, ulid, f_free);
     for (int i = 0; i < LBO_Q; ++i) {
         int sx = lbo_wrap(x - lbo_c[i][0], nx);
         int sy = lbo_wrap(y - lbo_c[i][1], ny);
         int sz = lbo_wrap(z - lbo_c[i][2], nz);
         size_t src = lbo_idx(sx, sy, sz, nx, ny);
+        if (flags != NULL && flags[src] == LBO_FARFIELD) {
+            f[i] = f_free[i];
+            continue;
+        }
         if (flags == NULL || flags[src] == LBO_FLUID) {
             f[i] = A[(size_t)i * N + src];
         } else {

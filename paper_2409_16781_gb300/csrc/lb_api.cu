@@ -157,7 +157,7 @@ int create_common(lb_lattice** out, int nx, int ny, int nz, double tau, const do
     const Layout L = layout_for(nx, ny, nz, o.storage, o.inplace);
     if (flags) {
         for (int64_t c = 0; c < L.N; ++c)
-            if (flags[c] > LB_LID) return fail(LB_EINVAL, "lb_create: flag %d at cell %lld", flags[c], (long long)c);
+            if (flags[c] > LB_FARFIELD) return fail(LB_EINVAL, "lb_create: flag %d at cell %lld", flags[c], (long long)c);
     }
     if (buffer) {
         if (bytes < L.total) return fail(LB_ENOMEM, "lb_create_in: buffer %zu < required %zu", bytes, L.total);

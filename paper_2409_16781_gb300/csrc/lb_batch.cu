@@ -717,7 +717,7 @@ int lb_batch_add(lb_batch* b, int nx, int ny, int nz, double tau, const double* 
     const int64_t N = (int64_t)nx * ny * nz;
     if (flags)
         for (int64_t c = 0; c < N; ++c)
-            if (flags[c] > LB_LID) return bfail(LB_EINVAL, "lb_batch_add: flag %d at cell %lld", flags[c], (long long)c);
+            if (flags[c] > LB_FARFIELD) return bfail(LB_EINVAL, "lb_batch_add: flag %d at cell %lld", flags[c], (long long)c);
     int slot = -1;
     for (int s = 0; s < b->max_slots; ++s)
         if (!b->slots[s].used) {

@@ -47,11 +47,12 @@ struct D3Q19 {
 };
 
 // Internal per-cell code byte (built from the user's flags at create time):
-//   bits 0-1: own type (0 fluid, 1 wall, 2 lid)
+//   bits 0-1: own type (0 fluid, 1 wall, 2 lid, 3 far field)
 //   bit 7   : some pull source x - c_i of this cell is solid, so the cell
 //             takes the bounce-back path (interior cells skip the 18
 //             neighbour-flag reads).
 constexpr uint8_t CODE_TYPE = 0x03;
+constexpr uint8_t CODE_FARFIELD = 0x03;
 constexpr uint8_t CODE_NEAR_WALL = 0x80;
 
 // Storage traits: populations are stored as deviations d_i = f_i - w_i.

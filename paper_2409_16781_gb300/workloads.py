@@ -9,7 +9,8 @@ only their inputs.
 
 Arrays use the layout of the library: a scalar field is (nz, ny, nx), a vector
 field is (3, nz, ny, nx), cell index x + nx*(y + ny*z).  Flag values: 0 fluid,
-1 wall (no-slip bounce-back), 2 lid (bounce-back from a wall moving at u_lid).
+1 wall (no-slip bounce-back), 2 lid (bounce-back from a wall moving at u_lid),
+3 far field (the free stream moving at u_lid: inflow / outflow planes).
 
 The workloads stand in for the paper's use cases (arXiv 2409.16781 Sec. 3.3:
 lid-driven cavity, Taylor-Green vortex, flow past an obstacle), extended to 3D.
@@ -21,7 +22,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-FLUID, WALL, LID = 0, 1, 2
+FLUID, WALL, LID, FARFIELD = 0, 1, 2, 3
 _MASK64 = (1 << 64) - 1
 
 
@@ -80,6 +81,22 @@ def channel_flags(nx: int, ny: int, nz: int, walls=("y",)) -> np.ndarray:
     if "z" in walls:
         f[0, :, :] = WALL
         f[nz - 1, :, :] = WALL
+    return f
+
+
+def cylinder_flags(nx: int, ny: int, nz: int, diameter: float, cx: float, cy: float) -> np.ndarray:
+    """Flow past a cylinder (the paper's von Karman street use case, in 3D):
+    a cylinder along z of the given diameter centred at (cx, cy) -- cell
+    (x, y, z) solid when (x - cx)^2 + (y - cy)^2 <= (diameter/2)^2 -- with
+    FARFIELD planes at x = 0 and x = nx-1 (inflow and outflow held at the
+    free stream) and periodic y and z (an unconfined cylinder, repeated
+    every ny cells)."""
+    f = np.zeros((nz, ny, nx), dtype=np.uint8)
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    r = 0.5 * diameter
+    f[:, (xx - cx) ** 2 + (yy - cy) ** 2 <= r * r] = WALL
+    f[:, :, 0] = FARFIELD
+    f[:, :, nx - 1] = FARFIELD
     return f
 
 

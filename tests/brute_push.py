@@ -56,7 +56,11 @@ def guo(tau, rho, u, g):
 
 class Brute:
     def __init__(self, nx, ny, nz, tau, u_lid, g, flags):
-        """flags: dict or callable (x,y,z) -> 0 fluid, 1 wall, 2 lid."""
+        """flags: callable (x,y,z) -> 0 fluid, 1 wall, 2 lid, 3 far field.
+
+        A far-field cell is the free stream: it absorbs what is pushed into
+        it and pushes, in every direction, the equilibrium of density 1
+        moving at u_lid."""
         self.n = (nx, ny, nz)
         self.tau = tau
         self.u_lid = tuple(u_lid)
@@ -77,12 +81,25 @@ class Brute:
                 kind = self.flag(*t)
                 if kind == 0:
                     incoming[t][i] = post[i]
+                elif kind == 3:
+                    pass  # absorbed by the free stream
                 else:
                     val = post[i]
                     if kind == 2:
                         # a moving wall hands back momentum 2 w_i rho_w (c.u_w)/cs^2
                         val -= 2.0 * WGT[i] * 1.0 * _dot(c, self.u_lid) / CS2
                     incoming[(x, y, z)][OPP[i]] = val
+        # far-field cells push the free-stream equilibrium into the fluid
+        f_free = feq(1.0, self.u_lid)
+        for z in range(nz):
+            for y in range(ny):
+                for x in range(nx):
+                    if self.flag(x, y, z) != 3:
+                        continue
+                    for i, c in enumerate(VEL):
+                        t = ((x + c[0]) % nx, (y + c[1]) % ny, (z + c[2]) % nz)
+                        if self.flag(*t) == 0:
+                            incoming[t][i] = f_free[i]
         # collide
         newP = {}
         for cell in self.fluid:

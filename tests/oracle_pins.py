@@ -343,8 +343,8 @@ def _to_brute_order(c_oracle):
 def pin_brute_force(lib=None):
     """Agreement with the push-form brute-force stepper on tiny grids:
     1x1x1 (pure collision), a 3x3x3 box with one fluid cell (pure
-    bounce-back off walls and lid), and a 3x5x7 random flag field with lid
-    and force."""
+    bounce-back off walls and lid), a 3x5x7 random flag field with lid
+    and force, and a 7x4x3 grid with far-field planes, walls and a lid."""
     from brute_push import Brute
     c, w = O.velocity_set(lib)
     perm = _to_brute_order(c)          # oracle index i -> brute index perm[i]
@@ -356,6 +356,12 @@ def pin_brute_force(lib=None):
     cases.append((3, 3, 3, 0.9, (0.07, -0.03, 0.0), (0, 0, 0), box))
     cases.append((3, 5, 7, 0.65, (0.05, 0.02, 0.0), (1e-4, 0, -1e-4),
                   W.random_flags(3, 5, 7, seed=9, p_wall=0.25, p_lid=0.15)))
+    # far-field planes (free stream at u_lid) at both x ends, walls and a lid
+    ff = W.random_flags(7, 4, 3, seed=4, p_wall=0.2, p_lid=0.1)
+    ff[:, :, 0] = W.FARFIELD
+    ff[:, :, 6] = W.FARFIELD
+    ff[1, 2, 3] = W.FARFIELD
+    cases.append((7, 4, 3, 0.75, (0.06, -0.02, 0.01), (0, 2e-4, 0), ff))
     rng = np.random.default_rng(17)
     for nx, ny, nz, tau, ulid, g, fl in cases:
         A = w[:, None, None, None] + 0.01 * (rng.random((19, nz, ny, nx)) - 0.5)
@@ -375,6 +381,71 @@ def pin_brute_force(lib=None):
             for i in range(19):
                 assert abs(L.A[i, z, y, x] - B.P[(x, y, z)][perm[i]]) < 1e-15, \
                     f"brute force disagrees at {(x, y, z)} dir {c[i]}"
+
+
+# ------------------------------------------------------------------ far field
+def _farfield_channel(nx, ny, nz, U, walls):
+    fl = np.zeros((nz, ny, nx), np.uint8)
+    if walls:
+        fl[:, 0, :] = W.WALL
+        fl[:, ny - 1, :] = W.WALL
+    fl[:, :, 0] = np.where(fl[:, :, 0] == 0, W.FARFIELD, fl[:, :, 0])
+    fl[:, :, nx - 1] = np.where(fl[:, :, nx - 1] == 0, W.FARFIELD, fl[:, :, nx - 1])
+    return fl
+
+
+def pin_farfield_free_stream(lib=None):
+    """Far-field planes at both ends of a box periodic in y, z hold the free
+    stream (rho = 1, u = U): the uniform flow is a fixed point (to rounding),
+    and a fluid started at rest becomes exactly that uniform flow (the only
+    steady state the two planes allow)."""
+    U = (0.05, 0.01, -0.02)
+    nx, ny, nz = 24, 3, 2
+    fl = _farfield_channel(nx, ny, nz, U, walls=False)
+    mask = fl == 0
+    L = O.Lattice(nx, ny, nz, 0.7, u_lid=U, flags=fl, lib=lib)
+    u0 = np.zeros((3, nz, ny, nx))
+    for a in range(3):
+        u0[a] = U[a]
+    L.init_fields(None, u0)
+    A0 = L.A.copy()
+    L.step(100)
+    assert np.abs(L.A[:, mask] - A0[:, mask]).max() < 1e-14, "uniform free stream is not a fixed point"
+    L = O.Lattice(nx, ny, nz, 0.7, u_lid=U, flags=fl, lib=lib)
+    L.step(4000)
+    rho, u = L.moments()
+    assert np.abs(rho[mask] - 1.0).max() < 1e-12, "density does not settle at 1"
+    for a in range(3):
+        assert np.abs(u[a][mask] - U[a]).max() < 1e-12, "velocity does not settle at U"
+
+
+def pin_farfield_channel_flux(lib=None):
+    """Walled channel (walls at y = 0, ny-1) between far-field planes: at
+    the steady state the mass carried across every plane x + 1/2 (the
+    populations that stream from column x to x + 1, minus those from x + 1
+    to x) is the same for every x -- the discrete continuity equation."""
+    U = (0.05, 0.0, 0.0)
+    nx, ny, nz = 24, 9, 1
+    fl = _farfield_channel(nx, ny, nz, U, walls=True)
+    c, _ = O.velocity_set(lib)
+    L = O.Lattice(nx, ny, nz, 0.8, u_lid=U, flags=fl, lib=lib)
+    L.step(6000)
+    J = []
+    for x in range(1, nx - 2):
+        s = 0.0
+        for z in range(nz):
+            for y in range(ny):
+                for i in range(19):
+                    cx, cy, cz = (int(v) for v in c[i])
+                    ty, tz = (y + cy) % ny, (z + cz) % nz
+                    if cx == 1 and fl[z, y, x] == 0 and fl[tz, ty, x + 1] == 0:
+                        s += L.A[i, z, y, x]
+                    if cx == -1 and fl[z, y, x + 1] == 0 and fl[tz, ty, x] == 0:
+                        s -= L.A[i, z, y, x + 1]
+        J.append(s)
+    J = np.array(J)
+    assert J.mean() > 0.1, "no flow through the channel"
+    assert (J.max() - J.min()) / J.mean() < 1e-10, f"mass flux varies along the channel: {J}"
 
 
 # ------------------------------------------------------------------ TRT
@@ -500,6 +571,8 @@ ALL_PINS = [
     pin_poiseuille,
     pin_cavity_mirror,
     pin_brute_force,
+    pin_farfield_free_stream,
+    pin_farfield_channel_flux,
     pin_trt_reduces_to_bgk,
     pin_trt_single_cell,
     pin_trt_conservation,

@@ -87,7 +87,7 @@ def test_create_rejects_bad_arguments(lib, args, what):
 def test_create_rejects_bad_flags(lib):
     h = ctypes.c_void_p()
     flags = np.zeros(64, dtype=np.uint8)
-    flags[17] = 3
+    flags[17] = 4  # 0..3 are fluid, wall, lid, far field
     st = lib.lb_create(ctypes.byref(h), 4, 4, 4, 0.7, None,
                        flags.ctypes.data_as(ctypes.c_void_p), None)
     assert st == L.LB_EINVAL

@@ -36,12 +36,17 @@ MIX = [
     (5, 31, 6, 0.8, "f16s", "cavity", 11),
     (64, 3, 2, 0.65, "f32", "random", 21),
     (15, 11, 7, 0.75, "f32d", "cavity", 19),
+    (30, 12, 3, 0.6, "f32", "cylinder", 45),
+    (28, 12, 4, 0.6, "f16s", "cylinder", 38),
 ]
 
 
 def _geom(nx, ny, nz, kind):
     if kind == "cavity":
         return W.cavity_flags(nx, ny, nz), (0.06, 0.0, 0.0), (0.0, 0.0, 0.0)
+    if kind == "cylinder":
+        return (W.cylinder_flags(nx, ny, nz, diameter=ny / 3, cx=nx / 3, cy=ny / 2 + 0.5), (0.05, 0.0, 0.0),
+                (0.0, 0.0, 0.0))
     if kind == "channel":
         return W.channel_flags(nx, ny, nz, walls=("y", "z")), (0.0, 0.0, 0.0), (2e-5, 0.0, 0.0)
     return W.random_flags(nx, ny, nz, seed=nx, p_wall=0.1, p_lid=0.05), (0.03, 0.01, 0.0), (1e-5, 0, 1e-5)

@@ -202,3 +202,17 @@ def test_inplace_memory_and_divergence():
     aa.step(1)
     with pytest.raises(LbDiverged):
         aa.totals()
+
+
+@pytest.mark.parametrize("steps", [300, 301])
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_inplace_flow_past_cylinder(storage, steps, perm):
+    """Far-field inflow / outflow planes in place: a pull from a far-field
+    cell reads no memory, so the in-place ownership argument still holds."""
+    nx, ny, nz, D = 64, 32, 3, 8
+    flags = W.cylinder_flags(nx, ny, nz, diameter=D, cx=2 * D, cy=ny / 2 + 0.5)
+    ora = O.Lattice(nx, ny, nz, 0.6, u_lid=(0.05, 0.0, 0.0), flags=flags)
+    aa = Lattice(nx, ny, nz, 0.6, u_lid=(0.05, 0.0, 0.0), flags=flags, storage=storage, inplace=True)
+    ora.step(steps)
+    aa.step(steps)
+    _check(ora, aa, storage, perm, flags)

@@ -289,3 +289,36 @@ def test_trt_equal_rates_is_bgk(perm):
         lat.init_fields(rho0, u0)
         lat.step(20)
     assert np.array_equal(a.populations(), b.populations())
+
+
+def _farfield_flags(nx, ny, nz, seed):
+    fl = W.random_flags(nx, ny, nz, seed=seed, p_wall=0.1, p_lid=0.05)
+    fl[:, :, 0] = W.FARFIELD
+    fl[:, :, nx - 1] = W.FARFIELD
+    rng = np.random.default_rng(seed)
+    fl.reshape(-1)[rng.integers(0, nx * ny * nz, size=3)] = W.FARFIELD
+    return fl
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14])
+@pytest.mark.parametrize("storage", STORAGES)
+def test_farfield_every_variant(storage, kernel, perm):
+    """Far-field cells (free stream at u_lid: inflow and outflow planes, and a
+    few scattered ones) with walls, lid and force, every kernel variant."""
+    for nx, ny, nz in ((34, 7, 6), (35, 6, 5), (48, 5, 4)):
+        flags = _farfield_flags(nx, ny, nz, seed=nx + 1)
+        rho0, u0 = W.random_fields(nx, ny, nz, seed=5, du=0.05, drho=0.02)
+        ora, gpu = run_pair(nx, ny, nz, 0.7, 12, storage, flags, (0.04, 0.01, -0.02), (1e-4, 0, 0),
+                            rho0, u0, kernel=kernel)
+        check_pair(ora, gpu, storage, perm, flags)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s"])
+def test_flow_past_cylinder(storage, perm):
+    """The von Karman street geometry (cylinder between far-field inflow and
+    outflow planes, periodic y and z) from rest, 400 steps, BGK and TRT."""
+    nx, ny, nz, D = 96, 48, 4, 12
+    flags = W.cylinder_flags(nx, ny, nz, diameter=D, cx=3 * D, cy=ny / 2 + 0.5)
+    for trt in (0.0, 3 / 16):
+        ora, gpu = run_pair(nx, ny, nz, 0.56, 400, storage, flags, (0.05, 0, 0), trt_magic=trt)
+        check_pair(ora, gpu, storage, perm, flags)

@@ -35,6 +35,9 @@ MUTANTS = {
     "trt_guo_odd_scale": ("(1.0 - 0.5 * wm) * gm", "(1.0 - 0.5 * wp) * gm"),
     "trt_guo_even_scale": ("(1.0 - 0.5 * wp) * gp", "(1.0 - 0.5 * wm) * gp"),
     "trt_odd_part_sign": ("fm = 0.5 * (f[i] - f[o])", "fm = 0.5 * (f[o] - f[i])"),
+    "farfield_as_wall": ("flags[src] == LBO_FARFIELD", "flags[src] == 99"),
+    "farfield_density": ("lbo_equilibrium(1.0, ulid, f_free)", "lbo_equilibrium(1.02, ulid, f_free)"),
+    "farfield_at_rest": ("lbo_equilibrium(1.0, ulid, f_free)", "lbo_equilibrium(1.0, (double[3]){0, 0, 0}, f_free)"),
     "layout_transposed": ("(size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * (size_t)z)",
                           "(size_t)y + (size_t)ny * ((size_t)x + (size_t)nx * (size_t)z)"),
 }
