@@ -38,7 +38,7 @@ METRIC = "D3Q19 MLUPS & fraction of HBM roofline; batched-serve p50/p99 vs plain
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2, "f32d": 4}
 FALLBACK_HBM_GBS = 6800.0
 # the files that make up the step kernel (hashed to tie ncu figures to it)
-STEP_SOURCES = ("lb_common.cuh", "lb_kernels.cuh", "lb_step.cu")
+STEP_SOURCES = ("lb_common.cuh", "lb_kernels.cuh", "lb_step.cu", "lb_inplace.cu")
 
 
 def bytes_per_update(storage: str) -> int:
@@ -226,16 +226,20 @@ def measured_peaks():
 
 
 def ncu_traffic(profile_key: str, variant=None):
-    """Per-launch DRAM bytes from a committed ncu summary, if it was taken
-    on the current kernel sources and for the kernel variant being timed."""
+    """Per-launch DRAM bytes (read + write) from the committed ncu figures,
+    if they were taken on the current kernel sources and for the kernel
+    variant being timed (profiles/traffic.json: per workload key, the source
+    hash and one figure per variant)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as fh:
             d = json.load(fh)
         rec = d.get(profile_key)
-        if rec and rec.get("source_hash") == kernel_source_hash() and \
-                (variant is None or rec.get("variant") == variant):
-            return rec.get("dram_bytes_per_launch")
+        if rec and rec.get("source_hash") == kernel_source_hash():
+            per = rec.get("variants", {})
+            hit = per.get(str(variant)) if variant is not None else None
+            if hit:
+                return hit.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
     return None
@@ -404,7 +408,7 @@ def forms_section(n, steps=200, device=None):
 
 # ---------------------------------------------------------------- serving
 def run_serving(n_requests, rate_multipliers=(2.0,), budget_gb=64.0, seed=16781, calib=16,
-                device=None):
+                device=None, tight_budget_gb=0.75):
     """Continuous-batching serving of a seeded Poisson stream of cavity /
     channel requests (sizes log-uniform 16^3..192^3, aspect <= 4, tau in
     [0.52, 1], steps in [200, 5000], FP32 / shifted-FP16 50/50), against the
@@ -438,6 +442,20 @@ def run_serving(n_requests, rate_multipliers=(2.0,), budget_gb=64.0, seed=16781,
         torch.cuda.synchronize()
         out["runs"].append({"rate_multiplier": mult, "rate_hz": round(mult * capacity, 3),
                             "batched": sb.summary(), "sequential_fp32": ss.summary()})
+    if tight_budget_gb:
+        # the same stream against a small HBM budget, where admission is bound
+        # by memory: slots with two population arrays vs in-place slots (one
+        # array, about half the bytes per request)
+        mult = rate_multipliers[-1]
+        reqs = W.request_stream(n=n_requests, rate_hz=mult * capacity, seed=seed)
+        tight = {"budget_gb": tight_budget_gb, "rate_multiplier": mult}
+        for name, inplace in (("two_arrays", False), ("in_place", True)):
+            be = BatchBackend(int(tight_budget_gb * (1 << 30)), max_slots=1024, device=device, inplace=inplace)
+            st = serve(reqs, be, policy="srpt", target_cells=4_000_000)
+            be.close()
+            torch.cuda.synchronize()
+            tight[name] = st.summary()
+        out["memory_bound"] = tight
     return out
 
 

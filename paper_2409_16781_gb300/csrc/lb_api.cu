@@ -115,6 +115,7 @@ LatticeParams params_of(const lb_lattice* h) {
         p.g[a] = h->g[a];
         p.ulid[a] = h->ulid[a];
     }
+    set_farfield(p);
     p.err = h->err;
     return p;
 }

@@ -749,6 +749,7 @@ int lb_batch_add(lb_batch* b, int nx, int ny, int nz, double tau, const double* 
         d.p.g[a] = o.force[a];
         d.p.ulid[a] = u_lid ? u_lid[a] : 0.0;
     }
+    set_farfield(d.p);
     d.p.err = b->err;
     d.div_x = make_fastdiv(nx);
     d.div_xy = make_fastdiv(nx * ny);

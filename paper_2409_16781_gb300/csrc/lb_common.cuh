@@ -103,9 +103,23 @@ struct LatticeParams {
     double omega;     // 1/tau: rate of the part of f even under c -> -c
     double omega_m;   // rate of the odd part (two-relaxation-time); = omega for BGK
     double g[3];      // body force per unit mass
-    double ulid[3];   // lid velocity
+    double ulid[3];   // lid velocity (and free-stream velocity of far-field cells)
+    double ff[19];    // far-field deviations f^eq_i(1, ulid) - w_i (set_farfield)
     int* err;         // device error word (bounded waits that gave up), or nullptr
 };
+
+// The free stream seen from a far-field cell (the inflow and outflow planes
+// of flow past an obstacle, the paper's von Karman street use case,
+// Sec. 3.3): the deviations f^eq_i(1, U) - w_i = w_i (3 c.U + 9/2 (c.U)^2 -
+// 3/2 U.U) of the equilibrium of Eq. 2-3 at density 1 and U = ulid, filled
+// on the host once per lattice so that kernels only read them.
+inline void set_farfield(LatticeParams& p) {
+    const double uu = p.ulid[0] * p.ulid[0] + p.ulid[1] * p.ulid[1] + p.ulid[2] * p.ulid[2];
+    for (int i = 0; i < 19; ++i) {
+        const double cu = D3Q19::cx(i) * p.ulid[0] + D3Q19::cy(i) * p.ulid[1] + D3Q19::cz(i) * p.ulid[2];
+        p.ff[i] = D3Q19::w(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    }
+}
 
 // Error bits a kernel may set in LatticeParams::err.
 constexpr int ERR_WAIT_TIMEOUT = 1;

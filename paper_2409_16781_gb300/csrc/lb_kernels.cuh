@@ -53,22 +53,12 @@ __device__ __forceinline__ void st_pop(S* p, S v) {
 // where the bounce-back of the next step finds it.
 enum { FORM_AB = 0, FORM_SWAPPED = 1, FORM_STREAMED = 2 };
 
-// The free stream seen from a far-field cell (the inflow and outflow planes
-// of flow past an obstacle, the paper's von Karman street use case,
-// Sec. 3.3): the deviation f^eq_i(1, U) - w_i of the equilibrium of Eq. 2-3
-// at density 1 and U = u_lid, w_i (3 c.U + 9/2 (c.U)^2 - 3/2 U.U).
-__device__ __forceinline__ double farfield_dev(int i, const LatticeParams& p) {
-    const double cu = D3Q19::cx(i) * p.ulid[0] + D3Q19::cy(i) * p.ulid[1] + D3Q19::cz(i) * p.ulid[2];
-    const double uu = p.ulid[0] * p.ulid[0] + p.ulid[1] * p.ulid[1] + p.ulid[2] * p.ulid[2];
-    return D3Q19::w(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-}
-
 // Streaming, pull form: d[i] <- P_i(x - c_i), with periodic wrap at the
 // domain edges; if the source is a solid cell, halfway bounce-back takes the
 // cell's own opposite post-collision value P_opp(i)(x), plus
 // 6 w_i (c_i . u_lid) when the source is a moving-lid cell (wall density 1);
-// a far-field source sends the free stream (farfield_dev), whatever the
-// fluid sends out.  FORM says where P lives (above).
+// a far-field source sends the free stream (p.ff, set_farfield), whatever
+// the fluid sends out.  FORM says where P lives (above).
 template <class S, int HINT = 0, int FORM = FORM_AB>
 __device__ __forceinline__ void pull_cell(const S* __restrict__ A, const uint8_t* __restrict__ code,
                                           const LatticeParams& p, int x, int y, int z, int cell,
@@ -106,7 +96,7 @@ __device__ __forceinline__ void pull_cell(const S* __restrict__ A, const uint8_t
             if (t == 0) {
                 d[i] = fluid_src(i, src);
             } else if (t == CODE_FARFIELD) {
-                d[i] = (M)farfield_dev(i, p);
+                d[i] = (M)p.ff[i];
             } else {
                 M v = own_opp(i, src);
                 if (t == 2) {
@@ -139,7 +129,7 @@ __device__ __forceinline__ void bounce_fix(const S* __restrict__ A, const uint8_
         const int src = xs[D3Q19::cx(i) + 1] + ys[D3Q19::cy(i) + 1] + zs[D3Q19::cz(i) + 1];
         const uint8_t t = code[src] & CODE_TYPE;
         if (t == CODE_FARFIELD) {
-            d[i] = (M)farfield_dev(i, p);
+            d[i] = (M)p.ff[i];
         } else if (t != 0) {
             M v = Storage<S>::load(ld_pop<HINT>(A + (int64_t)D3Q19::opp(i) * p.ps + cell));
             if (t == 2) {

@@ -188,6 +188,7 @@ extern "C" int lb_totals_static(const void* populations, int64_t plane_stride, c
         p.ulid[a] = u_lid ? u_lid[a] : 0.0;
         if (!std::isfinite(p.g[a]) || !std::isfinite(p.ulid[a])) return LB_EINVAL;
     }
+    set_farfield(p);
     double* scratch = nullptr;
     cudaError_t e = scratch_for_current_device(&scratch);
     if (e != cudaSuccess) return LB_ECUDA;
