@@ -182,7 +182,8 @@ int lb_get_populations_at(lb_lattice *h, const int64_t *cells, int n, double *ou
  * nx % 16 == 0; block size fixed); 13 two cells per thread collided together
  * in packed FP32 (f32x2) arithmetic (FP32 or 16-bit storage, even nx); 14
  * four cells per thread, collided as two packed pairs (16-bit storage,
- * nx % 4 == 0).  A variant that does not apply to the lattice runs
+ * nx % 4 == 0); 15 as 13 with fewer registers per thread and more warps.
+ * A variant that does not apply to the lattice runs
  * variant 1.  block = threads per block (0 = default; rounded down to whole
  * warps). */
 int lb_set_kernel(lb_lattice *h, int variant, int block);

@@ -434,7 +434,7 @@ int lb_get_populations_at(lb_lattice* h, const int64_t* cells, int n, double* ou
 
 int lb_set_kernel(lb_lattice* h, int variant, int block) {
     if (!h) return fail(LB_EINVAL, "lb_set_kernel: NULL handle");
-    if (variant < 0 || variant > 14 || block < 0 || block > 1024)
+    if (variant < 0 || variant > 15 || block < 0 || block > 1024)
         return fail(LB_EINVAL, "lb_set_kernel: bad variant %d / block %d", variant, block);
     h->kernel = variant;
     h->block = block;
@@ -517,6 +517,7 @@ int lb_autotune(lb_lattice* h, int reps, int* variant, int* block, float* ms_per
     }
     if ((sixteen || h->storage == LB_F32) && h->nx % 2 == 0) {
         for (int b : {32, 64, 128}) add(13, b);
+        for (int b : {64, 128}) add(15, b);
     }
     if (sixteen && h->nx % 16 == 0) {
         add(10, 0);

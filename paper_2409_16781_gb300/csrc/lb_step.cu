@@ -404,6 +404,8 @@ static cudaError_t step_quads16_t(const void* A, void* B, const uint8_t* code, c
 //       in variant 4.
 //   14: four cells per thread (16-bit storage, nx % 4 == 0); one 8-byte load
 //       per direction as in variant 8, the cells collided as two pairs.
+//   15: variant 13 in blocks of at most 128 threads capped at 64 registers
+//       (32 warps per SM; a few values spill to L1-backed local memory).
 // Cells next to a wall leave the packed form for the bounce-back fix-up of
 // each cell and re-enter it.
 // ---------------------------------------------------------------------------
@@ -444,8 +446,8 @@ __device__ __forceinline__ void bounce_fix_x2(const S* __restrict__ A, const uin
     for (int i = 0; i < Q; ++i) d[i] = f32x2(a[i], b[i]);
 }
 
-template <class S, bool FORCE, int HINT>
-__global__ void __launch_bounds__(256) step_kernel_pairs_x2(const S* __restrict__ A, S* __restrict__ B,
+template <class S, bool FORCE, int HINT, int MINB>
+__global__ void __launch_bounds__(256 / MINB, MINB == 1 ? 0 : 4 * MINB) step_kernel_pairs_x2(const S* __restrict__ A, S* __restrict__ B,
                                                             const uint8_t* __restrict__ code, LatticeParams p,
                                                             int xblocks) {
     using V = typename Vec2<S>::T;
@@ -500,12 +502,12 @@ __global__ void __launch_bounds__(256) step_kernel_pairs_x2(const S* __restrict_
     }
 }
 
-template <class S, int HINT>
+template <class S, int HINT, int MINB>
 static cudaError_t step_pairs_x2_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p, int block,
                                    cudaStream_t st) {
     int bx = block > 0 ? (block / 32) * 32 : 64;  // whole warps (the shuffles need all 32 lanes)
     if (bx < 32) bx = 32;
-    if (bx > 256) bx = 256;
+    if (bx > 256 / MINB) bx = 256 / MINB;
     const int pairs = p.nx / 2;
     const int need = ((pairs + 31) / 32) * 32;
     if (bx > need) bx = need;
@@ -513,9 +515,11 @@ static cudaError_t step_pairs_x2_t(const void* A, void* B, const uint8_t* code, 
     const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if (force)
-        step_kernel_pairs_x2<S, true, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+        step_kernel_pairs_x2<S, true, HINT, MINB>
+            <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     else
-        step_kernel_pairs_x2<S, false, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+        step_kernel_pairs_x2<S, false, HINT, MINB>
+            <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     return cudaGetLastError();
 }
 
@@ -1029,8 +1033,11 @@ static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* co
                                        : step_tma16_t<S, 1>(A, B, code, p, block, st);
             return step_rows_t<S, 0>(A, B, code, p, block, st);
         case 13:
+        case 15:
             if constexpr (std::is_same<S, float>::value || sizeof(S) == 2) {
-                if (pairs_ok) return step_pairs_x2_t<S, 0>(A, B, code, p, block, st);
+                if (pairs_ok)
+                    return variant == 13 ? step_pairs_x2_t<S, 0, 1>(A, B, code, p, block, st)
+                                         : step_pairs_x2_t<S, 0, 2>(A, B, code, p, block, st);
             }
             return step_rows_t<S, 0>(A, B, code, p, block, st);
         case 14:
@@ -1040,11 +1047,11 @@ static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* co
             return step_rows_t<S, 0>(A, B, code, p, block, st);
         case 0:
             // measured defaults on GB300 (256^3): FP32 one cell per thread in
-            // 64-thread blocks; FP64 two cells per thread; 16-bit storage four
-            // cells per thread collided as packed FP32 pairs
+            // 64-thread blocks; FP64 two cells per thread; 16-bit storage two
+            // cells per thread collided as a packed FP32 pair, 64 registers
             if constexpr (sizeof(S) == 2) {
+                if (pairs_ok) return step_pairs_x2_t<S, 0, 2>(A, B, code, p, block > 0 ? block : 64, st);
                 if (p.nx % 4 == 0) return step_quads16_x2_t<S, 0>(A, B, code, p, block > 0 ? block : 32, st);
-                if (pairs_ok) return step_pairs16_t<S, 0>(A, B, code, p, block > 0 ? block : 64, st);
             }
             if constexpr (sizeof(S) == 8) {
                 if (pairs_ok) return step_pairs_t<S, 0>(A, B, code, p, block > 0 ? block : 128, st);
