@@ -222,3 +222,69 @@ def test_cavity_64_vs_oracle(storage, tol):
     _, u_g = lat.moments()
     err = vel_err(u_g, u_o, fluid_mask(flags, (n, n, n)))
     assert err <= tol, f"{storage}: {err:.3e}"
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_von_karman_street_full(storage, perm):
+    """Flow past a cylinder at the size the bench times (1024 x 256 x 64,
+    D = 32, U = 0.05, Re = 100, far-field inflow and outflow planes),
+    autotuned kernel: from the free stream, 300 steps; the far-field planes
+    keep the density near 1 (the mean over the fluid within 1e-3), and one
+    step on sampled cells -- next to the cylinder and to both far-field
+    planes among them -- matches the oracle."""
+    nx, ny, nz, D, U = 1024, 256, 64, 32, 0.05
+    tau = 0.5 + 3.0 * U * D / 100.0
+    cx, cy = 8 * D, ny / 2 + 0.5
+    flags = W.cylinder_flags(nx, ny, nz, diameter=D, cx=cx, cy=cy)
+    lat = Lattice(nx, ny, nz, tau, u_lid=(U, 0, 0), flags=flags, storage=storage)
+    lat.autotune(reps=3, cache=False)
+    u0 = np.zeros((3, nz, ny, nx))
+    u0[0] = U
+    u0[0][flags != 0] = 0.0
+    lat.init_fields(None, u0)
+    del u0
+    lat.step(300)
+    m, p = lat.totals()
+    fluid = int((flags == 0).sum())
+    assert abs(m / fluid - 1.0) < 1e-3 and p[0] > 0
+    fl = flags.reshape(-1)
+    extra = []
+    for z in (nz // 2,):
+        extra.append(int(1 + nx * (ny // 3 + ny * z)))              # next to the inflow plane
+        extra.append(int(nx - 2 + nx * (2 * ny // 3 + ny * z)))     # next to the outflow plane
+        y = int(cy)
+        x = int(cx - D / 2) - 1
+        while fl[x + 1 + nx * (y + ny * z)] == 0:
+            x += 1
+        extra.append(int(x + nx * (y + ny * z)))                     # in front of the cylinder
+    sampled_step_parity(lat, flags, tau, (U, 0, 0), (0, 0, 0), perm, storage, n_samples=40, seed=4,
+                        extra_cells=extra)
+    lat.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16s"])
+def test_inplace_taylor_green_256(storage, perm):
+    """In-place lattice at the bench size (TGV 256^3, one population array):
+    20 steps match the oracle's energy (f32 2e-5, f16s 4e-3 relative: the
+    storage tolerances as energies), mass is conserved, and one step on
+    sampled cells matches the oracle from both layouts."""
+    n, tau = 256, 0.55
+    rho0, u0 = W.taylor_green_fields(n, n, n, u0=0.05)
+    lat = Lattice(n, n, n, tau, storage=storage, inplace=True)
+    lat.autotune(reps=4, cache=False)
+    lat.init_fields(rho0, u0)
+    m0, _ = lat.totals()
+    ora = O.Lattice(n, n, n, tau)
+    ora.init_fields(rho0, u0)
+    ora.step(20)
+    lat.step(20)
+    r, u = ora.moments()
+    e_o = 0.5 * np.sum(r * (u * u).sum(0))
+    del ora, r, u
+    tol = {"f32": 2e-5, "f16s": 4e-3}[storage]
+    assert abs(kinetic_energy(lat) / e_o - 1) < tol
+    m1, _ = lat.totals()
+    assert abs(m1 - m0) / m0 < (1e-6 if storage == "f32" else 1e-4)
+    sampled_step_parity(lat, None, tau, (0, 0, 0), (0, 0, 0), perm, storage, n_samples=24, seed=5)
+    sampled_step_parity(lat, None, tau, (0, 0, 0), (0, 0, 0), perm, storage, n_samples=24, seed=6)
+    lat.close()
