@@ -100,8 +100,9 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_step_kernel(const SlotDev
     const int n = *nact;
     if (n <= 0) return;
     const int total = off[n];
+    const int G = gridDim.x;
     int k = 0;
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    for (int item = blockIdx.x; item < total; item += G) {
         // the item's slot: largest k with off[k] <= item (items only grow)
         if (off[k + 1] <= item) {
             int lo = k + 1, hi = n - 1;
@@ -113,7 +114,15 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_step_kernel(const SlotDev
             k = lo;
         }
         const int slot = act[k];
-        if (remaining[slot] <= 0) continue;
+        if (remaining[slot] <= 0) {
+            // a paused or finished slot: jump to this block's first item past
+            // its range (schedulers keep many admitted slots paused, and
+            // walking their items one by one would cost every block a global
+            // load per item)
+            const int end = off[k + 1];
+            item = end + ((blockIdx.x - end) % G + G) % G - G;  // the loop adds G
+            continue;
+        }
         const SlotDev& sd = slots[slot];
         const int cell = (item - off[k]) * BATCH_THREADS + threadIdx.x;
         if (cell >= (int)sd.p.N) continue;
@@ -469,6 +478,7 @@ template <class S, bool INPLACE>
 static cudaError_t occupancy_of(int* per) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, batch_step_kernel<S, INPLACE>, BATCH_THREADS, 0);
 }
+
 
 // One batched step: the kernels of the types in use run concurrently on side
 // streams forked from the batch stream, then the advance kernel.

@@ -17,6 +17,7 @@
 
 #include "lb_internal.h"
 #include "lb_kernels.cuh"
+#include "lb_pairs.cuh"
 
 namespace lbgb {
 
@@ -50,35 +51,6 @@ __global__ void __launch_bounds__(512) step_kernel_rows(const S* __restrict__ A,
 // Cells next to a wall then replace the directions with solid sources
 // (bounce_fix); all lanes execute the shuffles, so the loads are uniform.
 // ---------------------------------------------------------------------------
-template <class S> struct Vec2;
-template <> struct Vec2<double> { using T = double2; };
-template <> struct Vec2<float> { using T = float2; };
-template <> struct Vec2<__half> { using T = __half2; };
-template <> struct Vec2<__nv_bfloat16> { using T = __nv_bfloat162; };
-
-template <class S> __device__ __forceinline__ void split2(const typename Vec2<S>::T& v, typename Storage<S>::math& a,
-                                                          typename Storage<S>::math& b);
-template <> __device__ __forceinline__ void split2<double>(const double2& v, double& a, double& b) { a = v.x; b = v.y; }
-template <> __device__ __forceinline__ void split2<float>(const float2& v, float& a, float& b) { a = v.x; b = v.y; }
-template <> __device__ __forceinline__ void split2<__half>(const __half2& v, float& a, float& b) {
-    const float2 f = __half22float2(v);
-    a = f.x;
-    b = f.y;
-}
-template <> __device__ __forceinline__ void split2<__nv_bfloat16>(const __nv_bfloat162& v, float& a, float& b) {
-    const float2 f = __bfloat1622float2(v);
-    a = f.x;
-    b = f.y;
-}
-template <class S> __device__ __forceinline__ typename Vec2<S>::T pack2(typename Storage<S>::math a,
-                                                                        typename Storage<S>::math b);
-template <> __device__ __forceinline__ double2 pack2<double>(double a, double b) { return make_double2(a, b); }
-template <> __device__ __forceinline__ float2 pack2<float>(float a, float b) { return make_float2(a, b); }
-template <> __device__ __forceinline__ __half2 pack2<__half>(float a, float b) { return __floats2half2_rn(a, b); }
-template <> __device__ __forceinline__ __nv_bfloat162 pack2<__nv_bfloat16>(float a, float b) {
-    return __floats2bfloat162_rn(a, b);
-}
-
 template <class S, bool FORCE, int HINT>
 __global__ void __launch_bounds__(256) step_kernel_pairs(const S* __restrict__ A, S* __restrict__ B,
                                                          const uint8_t* __restrict__ code, LatticeParams p,
@@ -409,97 +381,17 @@ static cudaError_t step_quads16_t(const void* A, void* B, const uint8_t* code, c
 // Cells next to a wall leave the packed form for the bounce-back fix-up of
 // each cell and re-enter it.
 // ---------------------------------------------------------------------------
-template <class S> __device__ __forceinline__ f32x2 to_x2(uint32_t w);  // two packed 16-bit values
-template <> __device__ __forceinline__ f32x2 to_x2<__half>(uint32_t w) {
-    f32x2 r;
-    r.v = __half22float2(*reinterpret_cast<const __half2*>(&w));
-    return r;
-}
-template <> __device__ __forceinline__ f32x2 to_x2<__nv_bfloat16>(uint32_t w) {
-    return f32x2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
-}
-template <class S> __device__ __forceinline__ uint32_t from_x2(f32x2 d);
-template <> __device__ __forceinline__ uint32_t from_x2<__half>(f32x2 d) {
-    const __half2 h = __float22half2_rn(d.v);
-    return *reinterpret_cast<const uint32_t*>(&h);
-}
-template <> __device__ __forceinline__ uint32_t from_x2<__nv_bfloat16>(f32x2 d) {
-    const __nv_bfloat162 h = __float22bfloat162_rn(d.v);
-    return *reinterpret_cast<const uint32_t*>(&h);
-}
-
-// Bounce-back fix-up of the cells of a packed pair whose codes say so.
-template <class S, int HINT>
-__device__ __forceinline__ void bounce_fix_x2(const S* __restrict__ A, const uint8_t* __restrict__ code,
-                                              const LatticeParams& p, int x0, int y, int z, int cell0, uint8_t c0,
-                                              uint8_t c1, f32x2 (&d)[Q]) {
-    if (!((c0 | c1) & CODE_NEAR_WALL)) return;
-    float a[Q], b[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        a[i] = d[i].v.x;
-        b[i] = d[i].v.y;
-    }
-    if (c0 & CODE_NEAR_WALL) bounce_fix<S, HINT>(A, code, p, x0, y, z, cell0, a);
-    if (c1 & CODE_NEAR_WALL) bounce_fix<S, HINT>(A, code, p, x0 + 1, y, z, cell0 + 1, b);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) d[i] = f32x2(a[i], b[i]);
-}
-
 template <class S, bool FORCE, int HINT, int MINB>
-__global__ void __launch_bounds__(256 / MINB, MINB == 1 ? 0 : 4 * MINB) step_kernel_pairs_x2(const S* __restrict__ A, S* __restrict__ B,
-                                                            const uint8_t* __restrict__ code, LatticeParams p,
-                                                            int xblocks) {
-    using V = typename Vec2<S>::T;
-    const int nx = p.nx, ny = p.ny, nz = p.nz;
+__global__ void __launch_bounds__(256 / MINB, MINB == 1 ? 0 : 4 * MINB)
+    step_kernel_pairs_x2(const S* __restrict__ A, S* __restrict__ B, const uint8_t* __restrict__ code, LatticeParams p,
+                         int xblocks) {
     const int xb = blockIdx.x % xblocks;
     const int row = blockIdx.x / xblocks;
-    const int y = row % ny;
-    const int z = row / ny;
     const int x0 = 2 * (xb * blockDim.x + threadIdx.x);
-    const bool active = x0 < nx;
+    const bool active = x0 < p.nx;
     const int xa = active ? x0 : 0;  // in-bounds address for idle lanes
-    const int lane = threadIdx.x & 31;
-    const int nxy = nx * ny;
-    const int yo[3] = {(y == ny - 1 ? 0 : y + 1) * nx, y * nx, (y == 0 ? ny - 1 : y - 1) * nx};
-    const int zo[3] = {(z == nz - 1 ? 0 : z + 1) * nxy, z * nxy, (z == 0 ? nz - 1 : z - 1) * nxy};
-    const int cell0 = xa + nx * row;
-    f32x2 d[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const S* rowp = A + (int64_t)i * p.ps + yo[D3Q19::cy(i) + 1] + zo[D3Q19::cz(i) + 1];
-        const V v = ld_pop<HINT>(reinterpret_cast<const V*>(rowp + xa));
-        float a, b;
-        split2<S>(v, a, b);
-        if (D3Q19::cx(i) == 0) {
-            d[i] = f32x2(a, b);
-        } else if (D3Q19::cx(i) == 1) {  // source x - 1
-            float prev = __shfl_up_sync(0xffffffffu, b, 1);
-            if (lane == 0 && active) prev = Storage<S>::load(ld_pop<HINT>(rowp + (x0 == 0 ? nx - 1 : x0 - 1)));
-            d[i] = f32x2(prev, a);
-        } else {  // source x + 1
-            float next = __shfl_down_sync(0xffffffffu, a, 1);
-            if (active && (lane == 31 || x0 + 2 >= nx))
-                next = Storage<S>::load(ld_pop<HINT>(rowp + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2)));
-            d[i] = f32x2(b, next);
-        }
-    }
-    if (!active) return;
-    const uint8_t c0 = code[cell0], c1 = code[cell0 + 1];
-    bounce_fix_x2<S, HINT>(A, code, p, x0, y, z, cell0, c0, c1, d);
-    relax_dev<f32x2, FORCE>(d, p);
-    const bool f0 = !(c0 & CODE_TYPE), f1 = !(c1 & CODE_TYPE);
-    if (f0 && f1) {
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-            st_pop<HINT>(reinterpret_cast<V*>(B + (int64_t)i * p.ps + cell0), pack2<S>(d[i].v.x, d[i].v.y));
-    } else {  // solid cells are never written
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            if (f0) st_pop<HINT>(B + (int64_t)i * p.ps + cell0, Storage<S>::store(d[i].v.x));
-            if (f1) st_pop<HINT>(B + (int64_t)i * p.ps + cell0 + 1, Storage<S>::store(d[i].v.y));
-        }
-    }
+    pair_x2_update<S, FORCE, HINT>(A, B, code, p, xa, row % p.ny, row / p.ny, xa + p.nx * row, threadIdx.x & 31,
+                                   active);
 }
 
 template <class S, int HINT, int MINB>
