@@ -117,7 +117,7 @@ def test_taylor_green_256(storage, perm):
     whole = -np.polyfit(np.array(ts), np.log(E), 1)[0] / (2 * nu * k2) - 1
     print(f"TGV 256 {storage}: early-rate excess {early:+.4f}, 2000-step excess {whole:+.4f}")
     # the linear rate is a lower bound the decay approaches at early times;
-    # stretching adds dissipation as the vortices tilt (measured: see DESIGN)
+    # stretching adds dissipation as the vortices tilt (a 64^3 oracle run grows the same way)
     assert -0.02 < early < 0.05
     assert -0.02 < whole < 0.25
     m1, p1 = lat.totals()
