@@ -97,10 +97,12 @@ typedef struct lb_options {
                           alternate between two layouts of the same array,
                           each thread writing exactly the values it read, so
                           the lattice needs half the population memory for
-                          the same bytes per update.  lb_step then ignores
-                          the variant (one cell per thread); values that
-                          lb_get_populations reports for solid cells are
-                          the rest state f = w. */
+                          the same bytes per update.  Its step kernels:
+                          variant 2, two cells per thread collided in
+                          packed FP32 (FP32 or 16-bit storage, nx even);
+                          any other variant one cell per thread.  Values
+                          that lb_get_populations reports for solid cells
+                          are the rest state f = w. */
     int reserved[5];
 } lb_options;
 

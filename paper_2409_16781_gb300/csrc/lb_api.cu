@@ -455,19 +455,26 @@ static int autotune_inplace(lb_lattice* h, int reps, int* variant, int* block, f
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const LatticeParams p = params_of(h);
-    const int blocks[] = {32, 64, 128, 256, 512};
+    struct Cand {
+        int v, b;
+    };
+    Cand cands[8];
+    int nc = 0;
+    for (int b : {32, 64, 128, 256, 512}) cands[nc++] = {1, b};
+    if (h->nx % 2 == 0 && (h->sbytes == 2 || h->storage == LB_F32))
+        for (int b : {32, 64, 128}) cands[nc++] = {2, b};
     int best = -1;
     float best_ms = 0.f;
     int form = h->form;
-    auto one = [&](int b) {
-        cudaError_t r = launch_step_inplace(h->storage, 1, h->pop[0], h->code, p, form, b, h->stream);
+    auto one = [&](const Cand& c) {
+        cudaError_t r = launch_step_inplace(h->storage, c.v, h->pop[0], h->code, p, form, c.b, h->stream);
         form = form == FORM_SWAPPED ? FORM_STREAMED : FORM_SWAPPED;
         return r;
     };
-    for (int c = 0; c < 5 && e == cudaSuccess; ++c) {
-        e = one(blocks[c]);
+    for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+        e = one(cands[c]);
         if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = one(blocks[c]);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = one(cands[c]);
         if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
@@ -486,8 +493,8 @@ static int autotune_inplace(lb_lattice* h, int reps, int* variant, int* block, f
     if (e1) cudaEventDestroy(e1);
     if (e != cudaSuccess) return cuda_fail(e, "lb_autotune");
     if (er != cudaSuccess) return cuda_fail(er, "lb_autotune: restore");
-    h->kernel = 1;
-    h->block = blocks[best];
+    h->kernel = cands[best].v;
+    h->block = cands[best].b;
     if (variant) *variant = h->kernel;
     if (block) *block = h->block;
     if (ms_per_step) *ms_per_step = best_ms / reps;

@@ -15,8 +15,11 @@
 //       x + c_i: both shifted by the velocity (x-shifts are one element off
 //       the warp's 128-byte segment, as in the two-array pull).
 // Mapping: one thread per cell, a block covers consecutive x of one row.
+#include <type_traits>
+
 #include "lb_internal.h"
 #include "lb_kernels.cuh"
+#include "lb_pairs.cuh"
 
 namespace lbgb {
 
@@ -40,6 +43,131 @@ __global__ void __launch_bounds__(512) step_kernel_inplace(const S* Ar, S* Aw, c
     inplace_update<S, FORCE, FORM>(Ar, Aw, code, p, x, y, z, cell, cc);
 }
 
+// ---------------------------------------------------------------------------
+// Two x-adjacent cells per thread (nx even; FP32 or 16-bit storage), the
+// pair collided in packed FP32 (f32x2), capped at 64 registers (blocks of at
+// most 128 threads, 8 per SM) like the two-array variant 15.
+//   from FORM_STREAMED: one aligned 2-vector load of plane i at the pair
+//     and one aligned 2-vector store into plane opp(i) at the pair;
+//   from FORM_SWAPPED: the pair's pulled values from plane opp(i) at
+//     x - c_i (aligned 2-vector loads, x-shifts by lane shuffles, as in the
+//     two-array pair kernel); each cell's result goes to plane i at x + c_i:
+//     one aligned 2-vector store where c_x = 0, one store per cell where the
+//     x-shift would break the alignment.
+// Solid cells of a pair store nothing (as in the one-cell kernel).
+// ---------------------------------------------------------------------------
+template <class S, bool FORCE, int FORM>
+__global__ void __launch_bounds__(128, 8) step_kernel_inplace_pairs(const S* Ar, S* Aw,
+                                                                    const uint8_t* __restrict__ code,
+                                                                    LatticeParams p, int xblocks) {
+    using V = typename Vec2<S>::T;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    const int xb = blockIdx.x % xblocks;
+    const int row = blockIdx.x / xblocks;
+    const int y = row % ny;
+    const int z = row / ny;
+    const int x0r = 2 * (xb * blockDim.x + threadIdx.x);
+    const bool active = x0r < nx;
+    const int x0 = active ? x0r : 0;  // in-bounds address for idle lanes
+    const int lane = threadIdx.x & 31;
+    const int nxy = nx * ny;
+    const int cell0 = x0 + nx * row;
+    f32x2 d[Q];
+    if constexpr (FORM == FORM_STREAMED) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            float a, b;
+            split2<S>(*reinterpret_cast<const V*>(Ar + (int64_t)i * p.ps + cell0), a, b);
+            d[i] = f32x2(a, b);
+        }
+    } else {
+        // pull from plane opp(i) at x - c_i
+        const int yo[3] = {(y == ny - 1 ? 0 : y + 1) * nx, y * nx, (y == 0 ? ny - 1 : y - 1) * nx};
+        const int zo[3] = {(z == nz - 1 ? 0 : z + 1) * nxy, z * nxy, (z == 0 ? nz - 1 : z - 1) * nxy};
+        const bool own_prev = lane == 0 || x0 == 0;
+        const bool own_next = lane == 31 || x0 + 2 >= nx;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const S* rowp = Ar + (int64_t)D3Q19::opp(i) * p.ps + yo[D3Q19::cy(i) + 1] + zo[D3Q19::cz(i) + 1];
+            float a, b;
+            split2<S>(*reinterpret_cast<const V*>(rowp + x0), a, b);
+            if (D3Q19::cx(i) == 0) {
+                d[i] = f32x2(a, b);
+            } else if (D3Q19::cx(i) == 1) {  // source x - 1
+                float prev = __shfl_up_sync(0xffffffffu, b, 1);
+                if (own_prev && active) prev = Storage<S>::load(rowp[x0 == 0 ? nx - 1 : x0 - 1]);
+                d[i] = f32x2(prev, a);
+            } else {  // source x + 1
+                float next = __shfl_down_sync(0xffffffffu, a, 1);
+                if (own_next && active) next = Storage<S>::load(rowp[x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2]);
+                d[i] = f32x2(b, next);
+            }
+        }
+    }
+    if (!active) return;
+    const uint8_t c0 = code[cell0], c1 = code[cell0 + 1];
+    const bool f0 = !(c0 & CODE_TYPE), f1 = !(c1 & CODE_TYPE);
+    if (!f0 && !f1) return;  // solid cells hold no values of their own
+    bounce_fix_x2<S, 0, FORM>(Ar, code, p, x0, y, z, cell0, c0, c1, d);
+    relax_dev<f32x2, FORCE>(d, p);
+    if constexpr (FORM == FORM_STREAMED) {
+        // -> FORM_SWAPPED: P_i(x) into plane opp(i) at x
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            S* q = Aw + (int64_t)D3Q19::opp(i) * p.ps + cell0;
+            if (f0 && f1) {
+                *reinterpret_cast<V*>(q) = pack2<S>(d[i].v.x, d[i].v.y);
+            } else {
+                if (f0) q[0] = Storage<S>::store(d[i].v.x);
+                if (f1) q[1] = Storage<S>::store(d[i].v.y);
+            }
+        }
+    } else {
+        // -> FORM_STREAMED: P_i(x) into plane i at x + c_i (periodic wrap)
+        const int yt[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
+        const int zt[3] = {(z == 0 ? nz - 1 : z - 1) * nxy, z * nxy, (z == nz - 1 ? 0 : z + 1) * nxy};
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            S* rowt = Aw + (int64_t)i * p.ps + yt[D3Q19::cy(i) + 1] + zt[D3Q19::cz(i) + 1];
+            if (D3Q19::cx(i) == 0) {
+                if (f0 && f1) {
+                    *reinterpret_cast<V*>(rowt + x0) = pack2<S>(d[i].v.x, d[i].v.y);
+                } else {
+                    if (f0) rowt[x0] = Storage<S>::store(d[i].v.x);
+                    if (f1) rowt[x0 + 1] = Storage<S>::store(d[i].v.y);
+                }
+            } else if (D3Q19::cx(i) == 1) {  // targets x0 + 1, x0 + 2
+                if (f0) rowt[x0 + 1] = Storage<S>::store(d[i].v.x);
+                if (f1) rowt[x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2] = Storage<S>::store(d[i].v.y);
+            } else {  // targets x0 - 1, x0
+                if (f0) rowt[x0 == 0 ? nx - 1 : x0 - 1] = Storage<S>::store(d[i].v.x);
+                if (f1) rowt[x0] = Storage<S>::store(d[i].v.y);
+            }
+        }
+    }
+}
+
+template <class S, int FORM>
+static cudaError_t step_inplace_pairs_form(void* A, const uint8_t* code, const LatticeParams& p, int block,
+                                           cudaStream_t st) {
+    int bx = block > 0 ? (block / 32) * 32 : 64;  // whole warps (the shuffles need all 32 lanes)
+    if (bx < 32) bx = 32;
+    if (bx > 128) bx = 128;
+    const int pairs = p.nx / 2;
+    const int need = ((pairs + 31) / 32) * 32;
+    if (bx > need) bx = need;
+    const int xblocks = (pairs + bx - 1) / bx;
+    const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
+    const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
+    if (force)
+        step_kernel_inplace_pairs<S, true, FORM>
+            <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);
+    else
+        step_kernel_inplace_pairs<S, false, FORM>
+            <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);
+    return cudaGetLastError();
+}
+
 template <class S, int FORM>
 static cudaError_t step_inplace_form(void* A, const uint8_t* code, const LatticeParams& p, int block,
                                      cudaStream_t st) {
@@ -58,10 +186,18 @@ static cudaError_t step_inplace_form(void* A, const uint8_t* code, const Lattice
     return cudaGetLastError();
 }
 
+// Variants of an in-place lattice: 2 = two cells per thread in packed FP32
+// (FP32 or 16-bit storage, nx even); anything else one cell per thread.
 template <class S>
 static cudaError_t step_inplace_t(int variant, void* A, const uint8_t* code, const LatticeParams& p, int form,
                                   int block, cudaStream_t st) {
-    (void)variant;  // one kernel family so far: one cell per thread
+    if constexpr (std::is_same<S, float>::value || sizeof(S) == 2) {
+        if (variant == 2 && p.nx % 2 == 0) {
+            if (form == FORM_SWAPPED) return step_inplace_pairs_form<S, FORM_SWAPPED>(A, code, p, block, st);
+            if (form == FORM_STREAMED) return step_inplace_pairs_form<S, FORM_STREAMED>(A, code, p, block, st);
+            return cudaErrorInvalidValue;
+        }
+    }
     if (form == FORM_SWAPPED) return step_inplace_form<S, FORM_SWAPPED>(A, code, p, block, st);
     if (form == FORM_STREAMED) return step_inplace_form<S, FORM_STREAMED>(A, code, p, block, st);
     return cudaErrorInvalidValue;

@@ -113,8 +113,8 @@ __device__ __forceinline__ void pull_cell(const S* __restrict__ A, const uint8_t
 // Bounce-back fix-up for a cell next to a wall: every direction whose pull
 // source x - c_i is solid takes the cell's own opposite value instead, plus
 // the moving-lid term for LID sources, or the free stream for far-field
-// sources (same rules as pull_cell).
-template <class S, int HINT = 0>
+// sources (same rules as pull_cell; FORM as there).
+template <class S, int HINT = 0, int FORM = FORM_AB>
 __device__ __forceinline__ void bounce_fix(const S* __restrict__ A, const uint8_t* __restrict__ code,
                                            const LatticeParams& p, int x, int y, int z, int cell,
                                            typename Storage<S>::math (&d)[Q]) {
@@ -131,7 +131,11 @@ __device__ __forceinline__ void bounce_fix(const S* __restrict__ A, const uint8_
         if (t == CODE_FARFIELD) {
             d[i] = (M)p.ff[i];
         } else if (t != 0) {
-            M v = Storage<S>::load(ld_pop<HINT>(A + (int64_t)D3Q19::opp(i) * p.ps + cell));
+            // the cell's own P_opp(i), wherever FORM keeps it
+            const S* q = FORM == FORM_AB         ? A + (int64_t)D3Q19::opp(i) * p.ps + cell
+                         : FORM == FORM_SWAPPED ? A + (int64_t)i * p.ps + cell
+                                                : A + (int64_t)D3Q19::opp(i) * p.ps + src;
+            M v = Storage<S>::load(ld_pop<HINT>(q));
             if (t == 2) {
                 const double cu = D3Q19::cx(i) * p.ulid[0] + D3Q19::cy(i) * p.ulid[1] + D3Q19::cz(i) * p.ulid[2];
                 v += (M)(6.0 * D3Q19::w(i) * cu);

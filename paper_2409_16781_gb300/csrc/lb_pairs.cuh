@@ -62,7 +62,7 @@ template <> __device__ __forceinline__ uint32_t from_x2<__nv_bfloat16>(f32x2 d) 
 }
 
 // Bounce-back fix-up of the cells of a packed pair whose codes say so.
-template <class S, int HINT>
+template <class S, int HINT, int FORM = FORM_AB>
 __device__ __forceinline__ void bounce_fix_x2(const S* __restrict__ A, const uint8_t* __restrict__ code,
                                               const LatticeParams& p, int x0, int y, int z, int cell0, uint8_t c0,
                                               uint8_t c1, f32x2 (&d)[Q]) {
@@ -73,8 +73,8 @@ __device__ __forceinline__ void bounce_fix_x2(const S* __restrict__ A, const uin
         a[i] = d[i].v.x;
         b[i] = d[i].v.y;
     }
-    if (c0 & CODE_NEAR_WALL) bounce_fix<S, HINT>(A, code, p, x0, y, z, cell0, a);
-    if (c1 & CODE_NEAR_WALL) bounce_fix<S, HINT>(A, code, p, x0 + 1, y, z, cell0 + 1, b);
+    if (c0 & CODE_NEAR_WALL) bounce_fix<S, HINT, FORM>(A, code, p, x0, y, z, cell0, a);
+    if (c1 & CODE_NEAR_WALL) bounce_fix<S, HINT, FORM>(A, code, p, x0 + 1, y, z, cell0 + 1, b);
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = f32x2(a[i], b[i]);
 }

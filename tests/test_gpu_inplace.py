@@ -60,16 +60,19 @@ def _flags(spec, nx, ny, nz):
     return W.cavity_flags(nx, ny, nz)
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("steps", [1, 2, 7, 12])
 @pytest.mark.parametrize("storage", STORAGES)
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}x{c[2]}")
-def test_inplace_matches_oracle_and_two_arrays(case, storage, steps, perm):
+def test_inplace_matches_oracle_and_two_arrays(case, storage, steps, kernel, perm):
+    """Kernel 2 (two cells per thread, packed FP32) applies to FP32 and
+    16-bit storage with even nx; elsewhere it runs the one-cell kernel."""
     nx, ny, nz, tau, spec, ulid, g = case
     flags = _flags(spec, nx, ny, nz)
     rho0, u0 = W.random_fields(nx, ny, nz, seed=nx * 100 + ny * 10 + nz, du=0.06, drho=0.02)
     ora = O.Lattice(nx, ny, nz, tau, u_lid=ulid, flags=flags, force=g)
     ora.init_fields(rho0, u0)
-    aa = Lattice(nx, ny, nz, tau, u_lid=ulid, flags=flags, storage=storage, force=g, inplace=True)
+    aa = Lattice(nx, ny, nz, tau, u_lid=ulid, flags=flags, storage=storage, force=g, inplace=True, kernel=kernel)
     ab = Lattice(nx, ny, nz, tau, u_lid=ulid, flags=flags, storage=storage, force=g, kernel=1)
     for lat in (aa, ab):
         lat.init_fields(rho0, u0)
@@ -85,17 +88,19 @@ def test_inplace_matches_oracle_and_two_arrays(case, storage, steps, perm):
     ab.close()
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("trt", [0.0, 3 / 16])
 @pytest.mark.parametrize("steps", [500, 501])
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16s"])
-def test_inplace_cavity_32(storage, steps, trt, perm):
+def test_inplace_cavity_32(storage, steps, trt, kernel, perm):
     """32^3 lid-driven cavity (tau 0.6, lid (0.1,0,0)), an even and an odd
-    number of steps, BGK and TRT."""
+    number of steps, BGK and TRT, one and two cells per thread."""
     n = 32
     flags = W.cavity_flags(n, n, n)
     om = O.trt_omega_minus(0.6, trt) if trt else None
     ora = O.Lattice(n, n, n, 0.6, u_lid=(0.1, 0, 0), flags=flags, omega_minus=om)
-    aa = Lattice(n, n, n, 0.6, u_lid=(0.1, 0, 0), flags=flags, storage=storage, inplace=True, trt_magic=trt)
+    aa = Lattice(n, n, n, 0.6, u_lid=(0.1, 0, 0), flags=flags, storage=storage, inplace=True, trt_magic=trt,
+                 kernel=kernel)
     ora.step(steps)
     aa.step(steps)
     _check(ora, aa, storage, perm, flags)
@@ -181,7 +186,7 @@ def test_inplace_autotune_keeps_state(storage, perm, tmp_path, monkeypatch):
     aa.step(3)  # odd layout
     f0 = aa.populations()
     v, b, ms = aa.autotune(reps=3)
-    assert v == 1 and b in (32, 64, 128, 256, 512) and ms > 0
+    assert v in (1, 2) and b in (32, 64, 128, 256, 512) and ms > 0
     assert np.array_equal(aa.populations(), f0)
     ora = O.Lattice(nx, ny, nz, 0.6, u_lid=(0.05, 0, 0), flags=flags)
     ora.step(3)
@@ -204,15 +209,17 @@ def test_inplace_memory_and_divergence():
         aa.totals()
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("steps", [300, 301])
-@pytest.mark.parametrize("storage", ["f64", "f32"])
-def test_inplace_flow_past_cylinder(storage, steps, perm):
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s"])
+def test_inplace_flow_past_cylinder(storage, steps, kernel, perm):
     """Far-field inflow / outflow planes in place: a pull from a far-field
     cell reads no memory, so the in-place ownership argument still holds."""
     nx, ny, nz, D = 64, 32, 3, 8
     flags = W.cylinder_flags(nx, ny, nz, diameter=D, cx=2 * D, cy=ny / 2 + 0.5)
     ora = O.Lattice(nx, ny, nz, 0.6, u_lid=(0.05, 0.0, 0.0), flags=flags)
-    aa = Lattice(nx, ny, nz, 0.6, u_lid=(0.05, 0.0, 0.0), flags=flags, storage=storage, inplace=True)
+    aa = Lattice(nx, ny, nz, 0.6, u_lid=(0.05, 0.0, 0.0), flags=flags, storage=storage, inplace=True,
+                 kernel=kernel)
     ora.step(steps)
     aa.step(steps)
     _check(ora, aa, storage, perm, flags)
