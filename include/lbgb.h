@@ -166,10 +166,26 @@ int lb_totals(lb_lattice *h, double *mass, double *mom);
 
 /* Copy the post-collision populations (array A: the state after the last
  * step) to/from host FP64, q-major f[i*N + cell], library velocity order.
- * Values are exact conversions of the stored values (set: rounded to the
- * storage type, to nearest even, as deviations f - w for the S forms). */
+ * get: f = w_i + d_i of the stored deviation d_i, rounded to FP64 (exact
+ * unless d_i carries bits below FP64's resolution at w_i, which only FP64
+ * storage does); set: d_i = f - w_i rounded to the storage type, to nearest
+ * even.  So set(get()) reproduces FP32 and 16-bit states exactly and FP64
+ * states to within one FP64 rounding; lb_checkpoint_* below is exact for
+ * every form. */
 int lb_get_populations(lb_lattice *h, double *f);
 int lb_set_populations(lb_lattice *h, const double *f);
+
+/* Checkpoint / restart, bit-exact: the stored values of the current
+ * population array verbatim (19 planes of N values of the storage type),
+ * behind a 64-byte header with the dims, storage, layout (in place) and
+ * step count.  lb_checkpoint_bytes gives the buffer size (0 for NULL);
+ * save fills a host buffer of at least that size; load restores it into a
+ * lattice of the same dims, storage and population scheme (LB_EINVAL
+ * otherwise), layout and step count included.  Both synchronise the
+ * lattice's stream. */
+size_t lb_checkpoint_bytes(lb_lattice *h);
+int lb_checkpoint_save(lb_lattice *h, void *host, size_t bytes);
+int lb_checkpoint_load(lb_lattice *h, const void *host, size_t bytes);
 
 /* Populations of n listed cells (cell indices in [0, N)): out[k*19 + i].
  * For sampled checks on lattices too large to copy whole. */
@@ -314,6 +330,17 @@ int lb_batch_sync(lb_batch *b);
 int lb_batch_destroy(lb_batch *b);
 /* Description of the last batch failure on the calling thread. */
 const char *lb_batch_last_error(void);
+
+/* Self-test of the bounded device-side wait (no counterpart in the paper):
+ * the TMA pipeline step kernels (variants 10-12) wait on shared-memory
+ * barriers for their bulk copies, and each wait gives up after a deadline
+ * and reports (LB_ETIMEOUT from lb_sync) rather than hang the GPU.  This
+ * call runs that same wait on a barrier that nothing signals, with a
+ * deadline of `seconds` (0 < seconds <= 5), on `stream` (cudaStream_t or
+ * NULL), and synchronises it.  Returns LB_ETIMEOUT when the wait gave up
+ * as designed (the expected result), LB_EINVAL for a bad deadline,
+ * LB_ENOMEM / LB_ECUDA on CUDA failures.  The device context stays usable. */
+int lb_selftest_wait(double seconds, void *stream);
 
 /* Wait for all work issued on the lattice's stream.  Returns LB_ETIMEOUT
  * (and clears the condition) if a kernel's bounded wait on an asynchronous

@@ -60,6 +60,9 @@ SIGNATURES = {
     "lb_get_populations": (_I, [_P, _P]),
     "lb_set_populations": (_I, [_P, _P]),
     "lb_get_populations_at": (_I, [_P, _P, _I, _P]),
+    "lb_checkpoint_bytes": (_S, [_P]),
+    "lb_checkpoint_save": (_I, [_P, _P, _S]),
+    "lb_checkpoint_load": (_I, [_P, _P, _S]),
     "lb_set_kernel": (_I, [_P, _I, _I]),
     "lb_autotune": (_I, [_P, _I, _P, _P, _P]),
     "lb_totals_static": (_I, [_P, _I64, _P, _I, _I, _I, _I, _P, _P, _P, _P]),
@@ -84,6 +87,7 @@ SIGNATURES = {
     "lb_batch_sync": (_I, [_P]),
     "lb_batch_destroy": (_I, [_P]),
     "lb_batch_last_error": (ctypes.c_char_p, []),
+    "lb_selftest_wait": (_I, [_D, _P]),
     "lb_sync": (_I, [_P]),
     "lb_query": (_I, [_P, _P, _P, _P]),
     "lb_destroy": (_I, [_P]),

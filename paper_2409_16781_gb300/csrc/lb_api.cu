@@ -432,6 +432,65 @@ int lb_get_populations_at(lb_lattice* h, const int64_t* cells, int n, double* ou
     return LB_OK;
 }
 
+// Checkpoint: a 64-byte header, then the stored values of the current
+// population array verbatim, plane by plane (19 planes of N values).
+struct CheckpointHeader {
+    char magic[8];
+    int32_t nx, ny, nz, storage, inplace, form;
+    int64_t steps;
+    int32_t sbytes, reserved[5];
+};
+static_assert(sizeof(CheckpointHeader) == 64, "checkpoint header layout");
+
+size_t lb_checkpoint_bytes(lb_lattice* h) {
+    if (!h) return 0;
+    return sizeof(CheckpointHeader) + (size_t)Q * h->N * h->sbytes;
+}
+
+int lb_checkpoint_save(lb_lattice* h, void* host, size_t bytes) {
+    if (!h || !host) return fail(LB_EINVAL, "lb_checkpoint_save: NULL argument");
+    if (bytes < lb_checkpoint_bytes(h)) return fail(LB_EINVAL, "lb_checkpoint_save: buffer too small");
+    CheckpointHeader hd;
+    memset(&hd, 0, sizeof hd);
+    memcpy(hd.magic, "LBGBCKP1", 8);
+    hd.nx = h->nx;
+    hd.ny = h->ny;
+    hd.nz = h->nz;
+    hd.storage = h->storage;
+    hd.inplace = h->inplace;
+    hd.form = h->form;
+    hd.steps = h->steps;
+    hd.sbytes = h->sbytes;
+    memcpy(host, &hd, sizeof hd);
+    const size_t row = (size_t)h->N * h->sbytes;
+    cudaError_t e = cudaMemcpy2DAsync((char*)host + sizeof hd, row, h->pop[h->cur], (size_t)h->ps * h->sbytes, row, Q,
+                                      cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? LB_OK : cuda_fail(e, "lb_checkpoint_save");
+}
+
+int lb_checkpoint_load(lb_lattice* h, const void* host, size_t bytes) {
+    if (!h || !host) return fail(LB_EINVAL, "lb_checkpoint_load: NULL argument");
+    if (bytes < lb_checkpoint_bytes(h)) return fail(LB_EINVAL, "lb_checkpoint_load: buffer too small");
+    CheckpointHeader hd;
+    memcpy(&hd, host, sizeof hd);
+    if (memcmp(hd.magic, "LBGBCKP1", 8) != 0) return fail(LB_EINVAL, "lb_checkpoint_load: not a checkpoint");
+    if (hd.nx != h->nx || hd.ny != h->ny || hd.nz != h->nz || hd.storage != h->storage || hd.inplace != h->inplace ||
+        hd.sbytes != h->sbytes)
+        return fail(LB_EINVAL, "lb_checkpoint_load: checkpoint of a %d x %d x %d lattice (storage %d, inplace %d) "
+                    "does not fit this one", hd.nx, hd.ny, hd.nz, hd.storage, hd.inplace);
+    if (h->inplace && hd.form != FORM_SWAPPED && hd.form != FORM_STREAMED)
+        return fail(LB_EINVAL, "lb_checkpoint_load: bad layout");
+    const size_t row = (size_t)h->N * h->sbytes;
+    cudaError_t e = cudaMemcpy2DAsync(h->pop[h->cur], (size_t)h->ps * h->sbytes, (const char*)host + sizeof hd, row,
+                                      row, Q, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lb_checkpoint_load");
+    if (h->inplace) h->form = hd.form;
+    h->steps = hd.steps;
+    return LB_OK;
+}
+
 int lb_set_kernel(lb_lattice* h, int variant, int block) {
     if (!h) return fail(LB_EINVAL, "lb_set_kernel: NULL handle");
     if (variant < 0 || variant > 15 || block < 0 || block > 1024)

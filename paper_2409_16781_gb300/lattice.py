@@ -182,6 +182,20 @@ class Lattice:
             raise ValueError("populations have the wrong size")
         L.check(self.lib.lb_set_populations(self._h, _dptr(f)), "lb_set_populations")
 
+    def checkpoint(self) -> bytes:
+        """Bit-exact snapshot of the state (lb_checkpoint_save)."""
+        n = int(self.lib.lb_checkpoint_bytes(self._h))
+        buf = np.empty(n, dtype=np.uint8)
+        L.check(self.lib.lb_checkpoint_save(self._h, _dptr(buf), n), "lb_checkpoint_save")
+        return buf.tobytes()
+
+    def restore(self, snapshot: bytes):
+        """Restore a snapshot taken by checkpoint() of a lattice of the same
+        dims, storage and population scheme (lb_checkpoint_load)."""
+        buf = np.frombuffer(snapshot, dtype=np.uint8)
+        L.check(self.lib.lb_checkpoint_load(self._h, _dptr(np.ascontiguousarray(buf)), int(buf.size)),
+                "lb_checkpoint_load")
+
     def populations_at(self, cells):
         cells = np.ascontiguousarray(cells, dtype=np.int64).reshape(-1)
         out = np.empty((cells.size, Q))

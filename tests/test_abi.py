@@ -134,3 +134,9 @@ def test_inplace_option(lib):
     h = ctypes.c_void_p()
     assert lib.lb_create(ctypes.byref(h), 8, 8, 8, 0.7, None, None, ctypes.byref(o)) == L.LB_EINVAL
     assert "inplace" in lib.lb_last_error().decode()
+
+
+def test_selftest_wait_rejects_bad_deadlines(lib):
+    """lb_selftest_wait validates its deadline before any device work."""
+    for bad in (0.0, -1.0, 6.0, float("nan")):
+        assert lib.lb_selftest_wait(bad, None) == L.LB_EINVAL

@@ -1,0 +1,110 @@
+"""Failure detection and recovery without a GPU fault (GPU).
+
+* A bounded device-side wait gives up and reports LB_ETIMEOUT (the wait of
+  the TMA pipeline kernels, run on a barrier that nothing signals), and the
+  device context stays usable afterwards.
+* A lattice that diverges inside a batch is reported (LB_EDIVERGED) while
+  the other lattices of the batch are unaffected, bitwise.
+* Checkpoint / restart (lb_checkpoint_save / lb_checkpoint_load) is exact:
+  k steps, save, load into a new lattice, N - k steps equals N steps,
+  bitwise, for every storage form and both population schemes; restarting
+  through the FP64 population export instead is exact for FP16 storage and
+  within FP64 rounding (f = w + d is not representable in general) for the
+  others.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from parity import fluid_mask
+from paper_2409_16781_gb300 import Lattice, LbDiverged
+from paper_2409_16781_gb300 import _lib as L
+from paper_2409_16781_gb300 import workloads as W
+from paper_2409_16781_gb300.batch import Batch
+
+pytestmark = pytest.mark.gpu
+
+
+def test_bounded_wait_reports_timeout():
+    lib = L.lib()
+    stream = torch.cuda.current_stream()
+    st = lib.lb_selftest_wait(0.05, ctypes.c_void_p(stream.cuda_stream))
+    assert st == L.LB_ETIMEOUT
+    # the context is still usable: a lattice steps and syncs cleanly
+    lat = Lattice(16, 8, 8, 0.7, storage="f16s", kernel=10)
+    lat.step(5)
+    lat.sync()
+    m, _ = lat.totals()
+    assert abs(m - 16 * 8 * 8) < 1e-3
+
+
+def test_divergence_is_isolated_in_a_batch():
+    dims = [(12, 10, 8), (16, 8, 6), (10, 10, 10)]
+    b = Batch(capacity_bytes=32 << 20, max_slots=4)
+    slots = [b.add(nx, ny, nz, 0.7, 20, u_lid=(0.05, 0, 0), flags=W.cavity_flags(nx, ny, nz), storage="f32")
+             for nx, ny, nz in dims]
+    nx, ny, nz = dims[1]
+    rho = np.ones((nz, ny, nx))
+    rho[3, 4, 5] = np.nan
+    b.init_fields(slots[1], rho, None)
+    b.step(20)
+    assert set(b.poll()) == set(slots)
+    with pytest.raises(LbDiverged):
+        b.totals(slots[1])
+    for k in (0, 2):
+        nx, ny, nz = dims[k]
+        flags = W.cavity_flags(nx, ny, nz)
+        alone = Lattice(nx, ny, nz, 0.7, u_lid=(0.05, 0, 0), flags=flags, storage="f32", kernel=1)
+        alone.step(20)
+        mask = fluid_mask(flags, alone.shape)
+        assert np.array_equal(b.populations(slots[k])[:, mask], alone.populations()[:, mask])
+        b.totals(slots[k])  # no divergence reported
+    b.close()
+
+
+@pytest.mark.parametrize("inplace", [False, True])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s", "bf16s", "f32d"])
+def test_checkpoint_restart_is_exact(storage, inplace):
+    nx, ny, nz, tau = 34, 12, 10, 0.65
+    flags = W.random_flags(nx, ny, nz, seed=6, p_wall=0.06, p_lid=0.03)
+    flags[:, :, 0] = W.FARFIELD
+    rho0, u0 = W.random_fields(nx, ny, nz, seed=8, du=0.04, drho=0.01)
+    kw = dict(u_lid=(0.04, 0.01, 0.0), flags=flags, storage=storage, force=(1e-5, 0, 0), inplace=inplace)
+    straight = Lattice(nx, ny, nz, tau, **kw)
+    straight.init_fields(rho0, u0)
+    straight.step(37)
+    first = Lattice(nx, ny, nz, tau, **kw)
+    first.init_fields(rho0, u0)
+    first.step(17)                     # odd: the streamed layout when in place
+    snap = first.checkpoint()
+    exported = first.populations()
+    first.close()
+    resumed = Lattice(nx, ny, nz, tau, **kw)
+    resumed.restore(snap)
+    assert resumed.query()[2] == 17
+    resumed.step(20)
+    mask = fluid_mask(flags, straight.shape)
+    f_s = straight.populations()
+    assert np.array_equal(resumed.populations()[:, mask], f_s[:, mask])
+    m_r, p_r = resumed.totals()
+    m_s, p_s = straight.totals()
+    assert m_r == m_s and np.array_equal(p_r, p_s)
+    # through the FP64 export: exact for FP16 storage, FP64 rounding otherwise
+    via = Lattice(nx, ny, nz, tau, **kw)
+    via.set_populations(exported)
+    via.step(20)
+    f_v = via.populations()
+    if storage == "f16s":
+        assert np.array_equal(f_v[:, mask], f_s[:, mask])
+    else:
+        tol = {"f64": 1e-14, "f32": 1e-6, "f32d": 1e-6, "bf16s": 1e-2}[storage]
+        assert np.abs(f_v[:, mask] - f_s[:, mask]).max() < tol
+    # a checkpoint does not load into a lattice of another shape or scheme
+    other = Lattice(nx, ny, nz + 1, tau, storage=storage, inplace=inplace)
+    with pytest.raises(L.LbError):
+        other.restore(snap)
+    scheme = Lattice(nx, ny, nz, tau, **{**kw, "inplace": not inplace})
+    with pytest.raises(L.LbError):
+        scheme.restore(snap)
