@@ -505,17 +505,32 @@ def oracle_threads():
     return int(v) if v else (os.cpu_count() or 1)
 
 
-def cpu_baseline(n, budget_s=12.0):
+def cpu_baseline(n, budget_s=12.0, single_budget_s=4.0):
     """Oracle MLUPS on a bounded sample: an n x n x 16 slab, as many steps as
-    fit in about budget_s seconds (at least 2)."""
+    fit in about budget_s seconds (at least 2), on all host cores; and the
+    same on one thread (a child process with OMP_NUM_THREADS=1, a smaller
+    sample of about single_budget_s seconds)."""
     planes = 16
     t1, cells = oracle_slab_run(n, planes, 1)
     steps = max(2, min(200, int(budget_s / max(t1, 1e-3))))
     t, cells = oracle_slab_run(n, planes, steps)
-    return {"value": round(cells * steps / t / 1e6, 2), "unit": "MLUPS", "cores": oracle_threads(),
-            "kind": "oracle",
-            "sample": f"{steps} steps of a {n}x{n}x{planes} slab of the {n}^3 Taylor-Green lattice "
-                      f"(FP64 C oracle, OpenMP over z)"}
+    out = {"value": round(cells * steps / t / 1e6, 2), "unit": "MLUPS", "cores": oracle_threads(),
+           "kind": "oracle",
+           "sample": f"{steps} steps of a {n}x{n}x{planes} slab of the {n}^3 Taylor-Green lattice "
+                     f"(FP64 C oracle, OpenMP over z)"}
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "t1, c = bench.oracle_slab_run(%d, 4, 1); k = max(2, min(100, int(%f / max(t1, 1e-3)))); "
+            "t, c = bench.oracle_slab_run(%d, 4, k); print(json.dumps([c * k / t / 1e6, k]))"
+            % (ROOT, n, single_budget_s, n))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120,
+                           env={**os.environ, "OMP_NUM_THREADS": "1"})
+        v, k = json.loads(r.stdout.strip().splitlines()[-1])
+        out["single_thread"] = {"value": round(v, 2), "unit": "MLUPS", "cores": 1,
+                                "sample": f"{k} steps of a {n}x{n}x4 slab, OMP_NUM_THREADS=1"}
+    except (subprocess.SubprocessError, ValueError, IndexError, OSError):
+        out["single_thread"] = None
+    return out
 
 
 def run_reference(args, dist: Dist):
