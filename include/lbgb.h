@@ -191,7 +191,9 @@ int lb_checkpoint_load(lb_lattice *h, const void *host, size_t bytes);
  * For sampled checks on lattices too large to copy whole. */
 int lb_get_populations_at(lb_lattice *h, const int64_t *cells, int n, double *out);
 
-/* Step-kernel choice.  Variants: 0 library default; 1 one cell per thread;
+/* Step-kernel choice.  Variants: 0 library default (measured on GB300:
+ * FP32 and Mixed2 one cell per thread, FP64 two cells per thread, 16-bit
+ * storage variant 15); 1 one cell per thread;
  * 2, 3 as 1 with streaming / L2-only cache policies; 4, 5 two cells per
  * thread (even nx); 6, 7 two cells per thread, packed 16-bit registers
  * (16-bit storage, even nx); 8, 9 four cells per thread, packed 16-bit
@@ -202,8 +204,9 @@ int lb_get_populations_at(lb_lattice *h, const int64_t *cells, int n, double *ou
  * four cells per thread, collided as two packed pairs (16-bit storage,
  * nx % 4 == 0); 15 as 13 with fewer registers per thread and more warps.
  * A variant that does not apply to the lattice runs
- * variant 1.  block = threads per block (0 = default; rounded down to whole
- * warps). */
+ * variant 1.  In-place lattices have their own two kernels (see
+ * lb_options.inplace: variant 2 two cells per thread, others one).
+ * block = threads per block (0 = default; rounded down to whole warps). */
 int lb_set_kernel(lb_lattice *h, int variant, int block);
 
 /* Autotuner: time every applicable (variant, block) pair on this lattice
