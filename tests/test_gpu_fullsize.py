@@ -288,3 +288,33 @@ def test_inplace_taylor_green_256(storage, perm):
     sampled_step_parity(lat, None, tau, (0, 0, 0), (0, 0, 0), perm, storage, n_samples=24, seed=5)
     sampled_step_parity(lat, None, tau, (0, 0, 0), (0, 0, 0), perm, storage, n_samples=24, seed=6)
     lat.close()
+
+
+@pytest.mark.parametrize("storage,inplace,kernel", [("f16s", True, 2), ("f16s", False, 15)])
+def test_maximum_size(storage, inplace, kernel, perm):
+    """The largest lattice the library accepts (just under 2^31 cells:
+    2048 x 1024 x 1023, a lid-driven cavity) in FP16 deviations, in place
+    (one array, ~84 GB) and with two arrays (~165 GB): cell indices, plane
+    offsets and launch grids at their limits.  Mass from the FP64 reduction
+    stays at the fluid count, and one step on sampled cells -- the last
+    cells of the lattice and cells next to the lid among them -- matches
+    the oracle."""
+    import torch
+    nx, ny, nz = 2048, 1024, 1023
+    assert nx * ny * nz < 2 ** 31
+    flags = W.cavity_flags(nx, ny, nz)
+    fluid = (nx - 2) * (ny - 2) * (nz - 2)
+    lat = Lattice(nx, ny, nz, 0.6, u_lid=(0.1, 0, 0), flags=flags, storage=storage, inplace=inplace,
+                  kernel=kernel, block=64)
+    lat.step(3)
+    m, _ = lat.totals()
+    assert abs(m - fluid) < 1e-5 * fluid
+    last = nx * ny * nz - 1
+    extra = [int(last - nx * ny - nx - 1),                       # the last fluid cell
+             int((nx // 2) + nx * (ny // 2 + ny * (nz - 2))),    # under the lid
+             int((nx - 2) + nx * (1 + ny * (nz - 2)))]           # next to a wall and the lid
+    sampled_step_parity(lat, flags, 0.6, (0.1, 0, 0), (0, 0, 0), perm, storage, n_samples=16, seed=9,
+                        extra_cells=extra)
+    lat.close()
+    del lat, flags
+    torch.cuda.empty_cache()
