@@ -75,9 +75,12 @@ def parse_args(argv=None):
     ap.add_argument("--vks-steps", type=int, default=40000,
                     help="steps of the von Karman street run that measures the shedding frequency")
     ap.add_argument("--taus", default="0.52,0.56,0.6", help="relaxation times of the precision study")
-    ap.add_argument("--serve-requests", type=int, default=80,
-                    help="requests in the serving section of the default line (0 = skip)")
+    ap.add_argument("--serve-requests", type=int, default=None,
+                    help="requests of the serving run: default 80 in the default line's serving section "
+                         "(0 = skip it), 2000 for --workload serve")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="HBM budget of the batch pool")
+    ap.add_argument("--serve-tight-gb", type=float, default=0.75,
+                    help="HBM budget of the memory-bound serving comparison (two arrays vs in place; 0 = skip)")
     return ap.parse_args(argv)
 
 
@@ -590,8 +593,10 @@ def main(argv=None):
         line = run_ours(args, dist)
         if dist.rank == 0 and dist.world == 1 and not args.no_forms:
             line["other_forms"] = forms_section(args.n)
-        if dist.rank == 0 and dist.world == 1 and args.serve_requests > 0:
-            line["serving"] = run_serving(args.serve_requests, (2.0,), args.serve_budget_gb)
+        n_serve = 80 if args.serve_requests is None else args.serve_requests
+        if dist.rank == 0 and dist.world == 1 and n_serve > 0:
+            line["serving"] = run_serving(n_serve, (2.0,), args.serve_budget_gb,
+                                          tight_budget_gb=args.serve_tight_gb)
         elif dist.rank == 0:
             line["serving"] = None
         if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
@@ -812,8 +817,8 @@ def precision_line(args):
 def serve_line(args):
     """A full serving run: the request stream at 0.5x and 2x the sequential
     FP32 capacity; value = batched aggregate MLUPS at 2x."""
-    n = args.serve_requests if args.serve_requests > 0 else 2000
-    sv = run_serving(n, (0.5, 2.0), args.serve_budget_gb)
+    n = args.serve_requests if args.serve_requests else 2000
+    sv = run_serving(n, (0.5, 2.0), args.serve_budget_gb, tight_budget_gb=args.serve_tight_gb)
     hi = sv["runs"][-1]
     return {"metric": METRIC, "value": hi["batched"]["mlups"], "unit": "MLUPS", "n_gpus": 1,
             "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak",
