@@ -202,7 +202,11 @@ int lb_get_populations_at(lb_lattice *h, const int64_t *cells, int n, double *ou
  * nx % 16 == 0; block size fixed); 13 two cells per thread collided together
  * in packed FP32 (f32x2) arithmetic (FP32 or 16-bit storage, even nx); 14
  * four cells per thread, collided as two packed pairs (16-bit storage,
- * nx % 4 == 0); 15 as 13 with fewer registers per thread and more warps.
+ * nx % 4 == 0); 15 as 13 with fewer registers per thread and more warps;
+ * 16 as 1 and 17 as 15, each with the bounce-back of cells next to a wall
+ * reordered (all neighbour flags read first, then every value load issued
+ * together): same results, faster on lattices with many wall cells (porous
+ * media), a little slower elsewhere; 16 caps blocks at 128 threads.
  * A variant that does not apply to the lattice runs
  * variant 1.  In-place lattices have their own two kernels (see
  * lb_options.inplace: variant 2 two cells per thread, others one).

@@ -36,6 +36,7 @@ struct lb_lattice {
     cudaStream_t stream;
     int kernel, block;
     int64_t steps;
+    bool walls;  // some flag is not LB_FLUID: cells next to a wall exist
 };
 
 namespace {
@@ -156,9 +157,12 @@ int create_common(lb_lattice** out, int nx, int ny, int nz, double tau, const do
         if (u_lid && !std::isfinite(u_lid[a])) return fail(LB_EINVAL, "lb_create: non-finite u_lid");
     }
     const Layout L = layout_for(nx, ny, nz, o.storage, o.inplace);
+    bool walls = false;
     if (flags) {
-        for (int64_t c = 0; c < L.N; ++c)
+        for (int64_t c = 0; c < L.N; ++c) {
             if (flags[c] > LB_FARFIELD) return fail(LB_EINVAL, "lb_create: flag %d at cell %lld", flags[c], (long long)c);
+            walls |= flags[c] != LB_FLUID;
+        }
     }
     if (buffer) {
         if (bytes < L.total) return fail(LB_ENOMEM, "lb_create_in: buffer %zu < required %zu", bytes, L.total);
@@ -197,6 +201,7 @@ int create_common(lb_lattice** out, int nx, int ny, int nz, double tau, const do
     }
     char* b = (char*)h->base;
     h->inplace = o.inplace;
+    h->walls = walls;
     h->form = o.inplace ? FORM_SWAPPED : FORM_AB;
     h->pop[0] = b;
     h->pop[1] = o.inplace ? b : b + L.pop_bytes;
@@ -493,7 +498,7 @@ int lb_checkpoint_load(lb_lattice* h, const void* host, size_t bytes) {
 
 int lb_set_kernel(lb_lattice* h, int variant, int block) {
     if (!h) return fail(LB_EINVAL, "lb_set_kernel: NULL handle");
-    if (variant < 0 || variant > 15 || block < 0 || block > 1024)
+    if (variant < 0 || variant > 17 || block < 0 || block > 1024)
         return fail(LB_EINVAL, "lb_set_kernel: bad variant %d / block %d", variant, block);
     h->kernel = variant;
     h->block = block;
@@ -584,6 +589,10 @@ int lb_autotune(lb_lattice* h, int reps, int* variant, int* block, float* ms_per
     if ((sixteen || h->storage == LB_F32) && h->nx % 2 == 0) {
         for (int b : {32, 64, 128}) add(13, b);
         for (int b : {64, 128}) add(15, b);
+        if (h->walls) add(17, 64);
+    }
+    if (h->walls) {
+        for (int b : {64, 128}) add(16, b);
     }
     if (sixteen && h->nx % 16 == 0) {
         add(10, 0);

@@ -59,7 +59,13 @@ enum { FORM_AB = 0, FORM_SWAPPED = 1, FORM_STREAMED = 2 };
 // 6 w_i (c_i . u_lid) when the source is a moving-lid cell (wall density 1);
 // a far-field source sends the free stream (p.ff, set_farfield), whatever
 // the fluid sends out.  FORM says where P lives (above).
-template <class S, int HINT = 0, int FORM = FORM_AB>
+// MASK_FIRST changes only the order of work for cells next to a wall: all
+// 18 neighbour codes are loaded first (independent loads) into a bit mask of
+// solid sources, then every direction loads from its selected address (the
+// fluid source or the cell's own opposite value), so the 19 value loads are
+// in flight together instead of each waiting on its own code byte; lid and
+// far-field terms follow for the directions that need them.  Same values.
+template <class S, int HINT = 0, int FORM = FORM_AB, bool MASK_FIRST = false>
 __device__ __forceinline__ void pull_cell(const S* __restrict__ A, const uint8_t* __restrict__ code,
                                           const LatticeParams& p, int x, int y, int z, int cell,
                                           uint8_t cc, typename Storage<S>::math (&d)[Q]) {
@@ -88,6 +94,44 @@ __device__ __forceinline__ void pull_cell(const S* __restrict__ A, const uint8_t
             const int src = xs[D3Q19::cx(i) + 1] + ys[D3Q19::cy(i) + 1] + zs[D3Q19::cz(i) + 1];
             d[i] = fluid_src(i, src);
         }
+    } else if constexpr (MASK_FIRST) {
+        // all neighbour codes first (independent loads), then all 19 values
+        // from the selected addresses, then the rare lid / far-field terms
+        uint32_t solid = 0, special = 0;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const uint8_t t = code[xs[D3Q19::cx(i) + 1] + ys[D3Q19::cy(i) + 1] + zs[D3Q19::cz(i) + 1]] & CODE_TYPE;
+            solid |= (uint32_t)(t != 0) << i;
+            special |= (uint32_t)(t >= 2) << i;
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int src = xs[D3Q19::cx(i) + 1] + ys[D3Q19::cy(i) + 1] + zs[D3Q19::cz(i) + 1];
+            const bool b = (solid >> i) & 1u;
+            int64_t off;
+            if constexpr (FORM == FORM_AB)
+                off = b ? (int64_t)D3Q19::opp(i) * p.ps + cell : (int64_t)i * p.ps + src;
+            else if constexpr (FORM == FORM_SWAPPED)
+                off = b ? (int64_t)i * p.ps + cell : (int64_t)D3Q19::opp(i) * p.ps + src;
+            else
+                off = b ? (int64_t)D3Q19::opp(i) * p.ps + src : (int64_t)i * p.ps + cell;
+            d[i] = Storage<S>::load(ld_pop<HINT>(A + off));
+        }
+        if (special) {
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                if (!((special >> i) & 1u)) continue;
+                const int src = xs[D3Q19::cx(i) + 1] + ys[D3Q19::cy(i) + 1] + zs[D3Q19::cz(i) + 1];
+                const uint8_t t = code[src] & CODE_TYPE;
+                if (t == CODE_FARFIELD) {
+                    d[i] = (M)p.ff[i];
+                } else {
+                    const double cu = D3Q19::cx(i) * p.ulid[0] + D3Q19::cy(i) * p.ulid[1] +
+                                      D3Q19::cz(i) * p.ulid[2];
+                    d[i] += (M)(6.0 * D3Q19::w(i) * cu);
+                }
+            }
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
@@ -113,8 +157,8 @@ __device__ __forceinline__ void pull_cell(const S* __restrict__ A, const uint8_t
 // Bounce-back fix-up for a cell next to a wall: every direction whose pull
 // source x - c_i is solid takes the cell's own opposite value instead, plus
 // the moving-lid term for LID sources, or the free stream for far-field
-// sources (same rules as pull_cell; FORM as there).
-template <class S, int HINT = 0, int FORM = FORM_AB>
+// sources (same rules as pull_cell; FORM and MASK_FIRST as there).
+template <class S, int HINT = 0, int FORM = FORM_AB, bool MASK_FIRST = false>
 __device__ __forceinline__ void bounce_fix(const S* __restrict__ A, const uint8_t* __restrict__ code,
                                            const LatticeParams& p, int x, int y, int z, int cell,
                                            typename Storage<S>::math (&d)[Q]) {
@@ -124,6 +168,42 @@ __device__ __forceinline__ void bounce_fix(const S* __restrict__ A, const uint8_
     const int xs[3] = {x == nx - 1 ? 0 : x + 1, x, x == 0 ? nx - 1 : x - 1};
     const int ys[3] = {(y == ny - 1 ? 0 : y + 1) * nx, y * nx, (y == 0 ? ny - 1 : y - 1) * nx};
     const int zs[3] = {(z == nz - 1 ? 0 : z + 1) * nxy, z * nxy, (z == 0 ? nz - 1 : z - 1) * nxy};
+    if constexpr (MASK_FIRST) {
+        uint32_t solid = 0, special = 0;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const uint8_t t = code[xs[D3Q19::cx(i) + 1] + ys[D3Q19::cy(i) + 1] + zs[D3Q19::cz(i) + 1]] & CODE_TYPE;
+            solid |= (uint32_t)(t != 0) << i;
+            special |= (uint32_t)(t >= 2) << i;
+        }
+        if (!solid) return;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            if ((solid >> i) & 1u) {
+                const int src = xs[D3Q19::cx(i) + 1] + ys[D3Q19::cy(i) + 1] + zs[D3Q19::cz(i) + 1];
+                const S* q = FORM == FORM_AB         ? A + (int64_t)D3Q19::opp(i) * p.ps + cell
+                             : FORM == FORM_SWAPPED ? A + (int64_t)i * p.ps + cell
+                                                    : A + (int64_t)D3Q19::opp(i) * p.ps + src;
+                d[i] = Storage<S>::load(ld_pop<HINT>(q));
+            }
+        }
+        if (special) {
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                if (!((special >> i) & 1u)) continue;
+                const int src = xs[D3Q19::cx(i) + 1] + ys[D3Q19::cy(i) + 1] + zs[D3Q19::cz(i) + 1];
+                const uint8_t t = code[src] & CODE_TYPE;
+                if (t == CODE_FARFIELD) {
+                    d[i] = (M)p.ff[i];
+                } else {
+                    const double cu = D3Q19::cx(i) * p.ulid[0] + D3Q19::cy(i) * p.ulid[1] +
+                                      D3Q19::cz(i) * p.ulid[2];
+                    d[i] += (M)(6.0 * D3Q19::w(i) * cu);
+                }
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const int src = xs[D3Q19::cx(i) + 1] + ys[D3Q19::cy(i) + 1] + zs[D3Q19::cz(i) + 1];

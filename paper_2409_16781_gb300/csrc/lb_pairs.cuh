@@ -62,7 +62,7 @@ template <> __device__ __forceinline__ uint32_t from_x2<__nv_bfloat16>(f32x2 d) 
 }
 
 // Bounce-back fix-up of the cells of a packed pair whose codes say so.
-template <class S, int HINT, int FORM = FORM_AB>
+template <class S, int HINT, int FORM = FORM_AB, bool MASK_FIRST = false>
 __device__ __forceinline__ void bounce_fix_x2(const S* __restrict__ A, const uint8_t* __restrict__ code,
                                               const LatticeParams& p, int x0, int y, int z, int cell0, uint8_t c0,
                                               uint8_t c1, f32x2 (&d)[Q]) {
@@ -73,8 +73,8 @@ __device__ __forceinline__ void bounce_fix_x2(const S* __restrict__ A, const uin
         a[i] = d[i].v.x;
         b[i] = d[i].v.y;
     }
-    if (c0 & CODE_NEAR_WALL) bounce_fix<S, HINT, FORM>(A, code, p, x0, y, z, cell0, a);
-    if (c1 & CODE_NEAR_WALL) bounce_fix<S, HINT, FORM>(A, code, p, x0 + 1, y, z, cell0 + 1, b);
+    if (c0 & CODE_NEAR_WALL) bounce_fix<S, HINT, FORM, MASK_FIRST>(A, code, p, x0, y, z, cell0, a);
+    if (c1 & CODE_NEAR_WALL) bounce_fix<S, HINT, FORM, MASK_FIRST>(A, code, p, x0 + 1, y, z, cell0 + 1, b);
 #pragma unroll
     for (int i = 0; i < Q; ++i) d[i] = f32x2(a[i], b[i]);
 }
@@ -86,7 +86,7 @@ __device__ __forceinline__ void bounce_fix_x2(const S* __restrict__ A, const uin
 // comes from the previous lane's second cell and the value at x0+2 (c_x =
 // -1) from the next lane's first cell when that lane holds the same row;
 // otherwise (warp edge, row edge, periodic wrap) the lane loads it itself.
-template <class S, bool FORCE, int HINT>
+template <class S, bool FORCE, int HINT, bool MASK_FIRST = false>
 __device__ __forceinline__ void pair_x2_update(const S* __restrict__ A, S* __restrict__ B,
                                                const uint8_t* __restrict__ code, const LatticeParams& p, int x0,
                                                int y, int z, int cell0, int lane, bool active) {
@@ -119,7 +119,7 @@ __device__ __forceinline__ void pair_x2_update(const S* __restrict__ A, S* __res
     }
     if (!active) return;
     const uint8_t c0 = code[cell0], c1 = code[cell0 + 1];
-    bounce_fix_x2<S, HINT>(A, code, p, x0, y, z, cell0, c0, c1, d);
+    bounce_fix_x2<S, HINT, FORM_AB, MASK_FIRST>(A, code, p, x0, y, z, cell0, c0, c1, d);
     relax_dev<f32x2, FORCE>(d, p);
     const bool f0 = !(c0 & CODE_TYPE), f1 = !(c1 & CODE_TYPE);
     if (f0 && f1) {

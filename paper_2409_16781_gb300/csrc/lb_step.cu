@@ -22,10 +22,13 @@
 
 namespace lbgb {
 
-template <class S, bool FORCE, int HINT>
-__global__ void __launch_bounds__(512) step_kernel_rows(const S* __restrict__ A, S* __restrict__ B,
-                                                        const uint8_t* __restrict__ code, LatticeParams p,
-                                                        int xblocks) {
+// Variants 1-3 (and 16 with MASK_FIRST: cells next to a wall gather their
+// neighbour codes before any value, blocks of at most 128 threads capped at
+// 48 registers).
+template <class S, bool FORCE, int HINT, bool MASK_FIRST = false>
+__global__ void __launch_bounds__(MASK_FIRST ? 128 : 512, MASK_FIRST ? 10 : 0)
+    step_kernel_rows(const S* __restrict__ A, S* __restrict__ B, const uint8_t* __restrict__ code, LatticeParams p,
+                     int xblocks) {
     using M = typename Storage<S>::math;
     const int xb = blockIdx.x % xblocks;
     const int row = blockIdx.x / xblocks;
@@ -37,7 +40,7 @@ __global__ void __launch_bounds__(512) step_kernel_rows(const S* __restrict__ A,
     const uint8_t cc = code[cell];
     if (cc & CODE_TYPE) return;  // solid cells are never written
     M d[Q];
-    pull_cell<S, HINT>(A, code, p, x, y, z, cell, cc, d);
+    pull_cell<S, HINT, FORM_AB, MASK_FIRST>(A, code, p, x, y, z, cell, cc, d);
     relax_dev<M, FORCE>(d, p);
 #pragma unroll
     for (int i = 0; i < Q; ++i) st_pop<HINT>(B + (int64_t)i * p.ps + cell, Storage<S>::store(d[i]));
@@ -379,10 +382,12 @@ static cudaError_t step_quads16_t(const void* A, void* B, const uint8_t* code, c
 //       per direction as in variant 8, the cells collided as two pairs.
 //   15: variant 13 in blocks of at most 128 threads capped at 64 registers
 //       (32 warps per SM; a few values spill to L1-backed local memory).
+//   17: variant 15 with the mask-first bounce-back fix-up (MASK_FIRST:
+//       neighbour codes first, then the wall values together).
 // Cells next to a wall leave the packed form for the bounce-back fix-up of
 // each cell and re-enter it.
 // ---------------------------------------------------------------------------
-template <class S, bool FORCE, int HINT, int MINB>
+template <class S, bool FORCE, int HINT, int MINB, bool MASK_FIRST = false>
 __global__ void __launch_bounds__(256 / MINB, MINB == 1 ? 0 : 4 * MINB)
     step_kernel_pairs_x2(const S* __restrict__ A, S* __restrict__ B, const uint8_t* __restrict__ code, LatticeParams p,
                          int xblocks) {
@@ -391,11 +396,11 @@ __global__ void __launch_bounds__(256 / MINB, MINB == 1 ? 0 : 4 * MINB)
     const int x0 = 2 * (xb * blockDim.x + threadIdx.x);
     const bool active = x0 < p.nx;
     const int xa = active ? x0 : 0;  // in-bounds address for idle lanes
-    pair_x2_update<S, FORCE, HINT>(A, B, code, p, xa, row % p.ny, row / p.ny, xa + p.nx * row, threadIdx.x & 31,
-                                   active);
+    pair_x2_update<S, FORCE, HINT, MASK_FIRST>(A, B, code, p, xa, row % p.ny, row / p.ny, xa + p.nx * row,
+                                               threadIdx.x & 31, active);
 }
 
-template <class S, int HINT, int MINB>
+template <class S, int HINT, int MINB, bool MASK_FIRST = false>
 static cudaError_t step_pairs_x2_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p, int block,
                                    cudaStream_t st) {
     int bx = block > 0 ? (block / 32) * 32 : 64;  // whole warps (the shuffles need all 32 lanes)
@@ -408,10 +413,10 @@ static cudaError_t step_pairs_x2_t(const void* A, void* B, const uint8_t* code, 
     const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if (force)
-        step_kernel_pairs_x2<S, true, HINT, MINB>
+        step_kernel_pairs_x2<S, true, HINT, MINB, MASK_FIRST>
             <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     else
-        step_kernel_pairs_x2<S, false, HINT, MINB>
+        step_kernel_pairs_x2<S, false, HINT, MINB, MASK_FIRST>
             <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     return cudaGetLastError();
 }
@@ -503,7 +508,7 @@ static cudaError_t step_quads16_x2_t(const void* A, void* B, const uint8_t* code
     return cudaGetLastError();
 }
 
-template <class S, int HINT>
+template <class S, int HINT, bool MASK_FIRST = false>
 static cudaError_t step_rows_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p, int block,
                                cudaStream_t st);
 
@@ -822,12 +827,12 @@ static cudaError_t step_tma16_t(const void* A, void* B, const uint8_t* code, con
     return force ? launch_tma16<S, true, G>(A, B, code, p, g, st) : launch_tma16<S, false, G>(A, B, code, p, g, st);
 }
 
-template <class S, int HINT>
+template <class S, int HINT, bool MASK_FIRST>
 static cudaError_t step_rows_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p, int block,
                                cudaStream_t st) {
     int bx = block > 0 ? (block / 32) * 32 : 256;
     if (bx < 32) bx = 32;
-    if (bx > 512) bx = 512;
+    if (bx > (MASK_FIRST ? 128 : 512)) bx = MASK_FIRST ? 128 : 512;
     // shrink the block for narrow rows (multiple of 32)
     const int need = ((p.nx + 31) / 32) * 32;
     if (bx > need) bx = need;
@@ -835,9 +840,9 @@ static cudaError_t step_rows_t(const void* A, void* B, const uint8_t* code, cons
     const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if (force)
-        step_kernel_rows<S, true, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+        step_kernel_rows<S, true, HINT, MASK_FIRST><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     else
-        step_kernel_rows<S, false, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+        step_kernel_rows<S, false, HINT, MASK_FIRST><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     return cudaGetLastError();
 }
 
@@ -894,6 +899,12 @@ static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* co
         case 14:
             if constexpr (sizeof(S) == 2) {
                 if (p.nx % 4 == 0) return step_quads16_x2_t<S, 0>(A, B, code, p, block, st);
+            }
+            return step_rows_t<S, 0>(A, B, code, p, block, st);
+        case 16: return step_rows_t<S, 0, true>(A, B, code, p, block, st);
+        case 17:
+            if constexpr (std::is_same<S, float>::value || sizeof(S) == 2) {
+                if (pairs_ok) return step_pairs_x2_t<S, 0, 2, true>(A, B, code, p, block, st);
             }
             return step_rows_t<S, 0>(A, B, code, p, block, st);
         case 0:

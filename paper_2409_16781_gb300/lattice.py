@@ -54,7 +54,7 @@ class Lattice:
 
     Arrays follow the library's layout: scalar fields (nz, ny, nx), vector
     fields (3, nz, ny, nx), populations (19, nz, ny, nx) in the library's
-    velocity order; flags uint8 (nz, ny, nx) with 0 fluid, 1 wall, 2 lid.
+    velocity order; flags uint8 (nz, ny, nx) with 0 fluid, 1 wall, 2 lid, 3 far field.
     trt_magic: 0 = BGK collision; > 0 = two-relaxation-time collision with
     that magic parameter (lb_options.trt_magic).
     inplace: one population array updated in place (lb_options.inplace).
@@ -209,11 +209,18 @@ class Lattice:
     def autotune(self, reps: int = 20, cache: bool = True):
         """Pick the fastest step-kernel variant and block size for this
         lattice (lb_autotune), remembering the choice in a JSON file keyed by
-        GPU, storage, dims and forcing (LBGB_AUTOTUNE_CACHE, default
-        ~/.cache/lbgb/autotune.json).  Returns (variant, block, ms/step)."""
+        GPU, storage, dims, forcing and geometry (a digest of the flags: the
+        best kernel depends on how many cells are next to a wall)
+        (LBGB_AUTOTUNE_CACHE, default ~/.cache/lbgb/autotune.json).
+        Returns (variant, block, ms/step)."""
+        import hashlib
+
         import torch
+        fl = self._flags
+        geo = ("walls:" + hashlib.blake2b(fl.tobytes(), digest_size=8).hexdigest()
+               if fl is not None and fl.any() else "nowalls")
         key = "|".join([torch.cuda.get_device_name(self.device), str(self.storage),
-                        f"{self.nx}x{self.ny}x{self.nz}", "force" if self._force else "noforce"]
+                        f"{self.nx}x{self.ny}x{self.nz}", "force" if self._force else "noforce", geo]
                        + (["trt"] if self.trt_magic else []) + (["inplace"] if self.inplace else []))
         path = os.environ.get("LBGB_AUTOTUNE_CACHE",
                               os.path.join(os.path.expanduser("~"), ".cache", "lbgb", "autotune.json"))

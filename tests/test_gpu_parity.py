@@ -70,7 +70,7 @@ TINY = [
     (66, 5, 4, 0.7, 20, ("random", 22), (0.02, 0.0, 0.0), (0, 0, 0)),
 ]
 
-KERNELS = [1, 4, 6, 10, 14]
+KERNELS = [1, 4, 6, 10, 14, 16, 17]
 
 
 def _flags(spec, nx, ny, nz):
@@ -93,7 +93,7 @@ def test_tiny_grids(case, storage, kernel, perm):
     check_pair(ora, gpu, storage, perm, flags)
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17])
 @pytest.mark.parametrize("storage", STORAGES)
 def test_every_variant(storage, kernel, perm):
     """Every step-kernel variant (cache policies, one or two cells per
@@ -139,6 +139,19 @@ def test_porous_channel_small(storage, kernel, perm):
     flags = W.porous_flags(nx, ny, nz, n_spheres=12, r_min=3, r_max=6, seed=2409)
     ora, gpu = run_pair(nx, ny, nz, 0.8, 200, storage, flags, force=(1e-5, 0, 0), kernel=kernel)
     check_pair(ora, gpu, storage, perm, flags)
+
+
+def test_set_kernel_range():
+    """Variants 0..17 are accepted; anything else is rejected before any
+    launch, and the lattice keeps stepping with its previous choice."""
+    gpu = Lattice(10, 6, 4, 0.7, flags=W.random_flags(10, 6, 4, seed=2), storage="f32")
+    for v in range(18):
+        gpu.set_kernel(v, 64)
+    for bad in (-1, 18, 99):
+        with pytest.raises(RuntimeError):
+            gpu.set_kernel(bad, 0)
+    gpu.step(3)
+    gpu.close()
 
 
 def test_zero_steps_and_rest_state():
@@ -300,7 +313,7 @@ def _farfield_flags(nx, ny, nz, seed):
     return fl
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17])
 @pytest.mark.parametrize("storage", STORAGES)
 def test_farfield_every_variant(storage, kernel, perm):
     """Far-field cells (free stream at u_lid: inflow and outflow planes, and a
