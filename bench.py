@@ -79,6 +79,10 @@ def parse_args(argv=None):
                     help="requests of the serving run: default 80 in the default line's serving section "
                          "(0 = skip it), 2000 for --workload serve")
     ap.add_argument("--serve-budget-gb", type=float, default=64.0, help="HBM budget of the batch pool")
+    ap.add_argument("--serve-rates", default="0.5,2",
+                    help="arrival rates of --workload serve, as multiples of the sequential FP32 capacity")
+    ap.add_argument("--serve-max-wait", type=float, default=60.0,
+                    help="seconds after which a waiting request is served oldest-first (0 = no bound)")
     ap.add_argument("--serve-tight-gb", type=float, default=0.75,
                     help="HBM budget of the memory-bound serving comparison (two arrays vs in place; 0 = skip)")
     return ap.parse_args(argv)
@@ -411,7 +415,7 @@ def forms_section(n, steps=200, device=None):
 
 # ---------------------------------------------------------------- serving
 def run_serving(n_requests, rate_multipliers=(2.0,), budget_gb=64.0, seed=16781, calib=16,
-                device=None, tight_budget_gb=0.75):
+                device=None, tight_budget_gb=0.75, max_wait_s=60.0):
     """Continuous-batching serving of a seeded Poisson stream of cavity /
     channel requests (sizes log-uniform 16^3..192^3, aspect <= 4, tau in
     [0.52, 1], steps in [200, 5000], FP32 / shifted-FP16 50/50), against the
@@ -431,14 +435,16 @@ def run_serving(n_requests, rate_multipliers=(2.0,), budget_gb=64.0, seed=16781,
     capacity = len(cal) / max(st.makespan, 1e-9)      # requests per second
     out = {"requests": n_requests, "capacity_req_per_s": round(capacity, 3),
            "hbm_budget_gb": budget_gb, "storage_mix": "f32/f16s 50/50 (batched); f32 (sequential)",
-           "policy": "batched: shortest remaining work first, 4M-cell occupancy target, 8 ms chunks, "
-                     "3 queued; sequential: FIFO, one lattice at a time, one launch per step",
+           "policy": "batched: shortest remaining work first"
+                     + (f", requests waiting over {max_wait_s:g} s first (oldest first)" if max_wait_s else "")
+                     + ", 4M-cell occupancy target, 8 ms chunks, 3 queued; sequential: FIFO, one lattice "
+                       "at a time, one launch per step",
            "runs": []}
     out["f16s_accuracy"] = f16s_accuracy(base, samples=6, device=device)
     for mult in rate_multipliers:
         reqs = W.request_stream(n=n_requests, rate_hz=mult * capacity, seed=seed)
         be = BatchBackend(int(budget_gb * (1 << 30)), max_slots=1024, device=device)
-        sb = serve(reqs, be, policy="srpt", target_cells=4_000_000)
+        sb = serve(reqs, be, policy="srpt", target_cells=4_000_000, max_wait_s=max_wait_s)
         be.close()
         torch.cuda.synchronize()
         ss = serve(reqs, SequentialBackend("f32", device=device))
@@ -454,7 +460,7 @@ def run_serving(n_requests, rate_multipliers=(2.0,), budget_gb=64.0, seed=16781,
         tight = {"budget_gb": tight_budget_gb, "rate_multiplier": mult}
         for name, inplace in (("two_arrays", False), ("in_place", True)):
             be = BatchBackend(int(tight_budget_gb * (1 << 30)), max_slots=1024, device=device, inplace=inplace)
-            st = serve(reqs, be, policy="srpt", target_cells=4_000_000)
+            st = serve(reqs, be, policy="srpt", target_cells=4_000_000, max_wait_s=max_wait_s)
             be.close()
             torch.cuda.synchronize()
             tight[name] = st.summary()
@@ -596,7 +602,8 @@ def main(argv=None):
         n_serve = 80 if args.serve_requests is None else args.serve_requests
         if dist.rank == 0 and dist.world == 1 and n_serve > 0:
             line["serving"] = run_serving(n_serve, (2.0,), args.serve_budget_gb,
-                                          tight_budget_gb=args.serve_tight_gb)
+                                          tight_budget_gb=args.serve_tight_gb,
+                                          max_wait_s=args.serve_max_wait or None)
         elif dist.rank == 0:
             line["serving"] = None
         if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
@@ -818,7 +825,9 @@ def serve_line(args):
     """A full serving run: the request stream at 0.5x and 2x the sequential
     FP32 capacity; value = batched aggregate MLUPS at 2x."""
     n = args.serve_requests if args.serve_requests else 2000
-    sv = run_serving(n, (0.5, 2.0), args.serve_budget_gb, tight_budget_gb=args.serve_tight_gb)
+    rates = tuple(float(r) for r in args.serve_rates.split(","))
+    sv = run_serving(n, rates, args.serve_budget_gb, tight_budget_gb=args.serve_tight_gb,
+                     max_wait_s=args.serve_max_wait or None)
     hi = sv["runs"][-1]
     return {"metric": METRIC, "value": hi["batched"]["mlups"], "unit": "MLUPS", "n_gpus": 1,
             "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak",

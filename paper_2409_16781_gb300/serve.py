@@ -86,13 +86,19 @@ class Scheduler:
                 remaining work (cells x steps x bytes per update), in that
                 order, until ``target_cells`` cells are running; the others
                 stay resident but paused (backend.set_quotas).
+    ``max_wait_s`` (srpt only) bounds starvation: requests that arrived more
+    than ``max_wait_s`` seconds ago are granted first, oldest first, ahead of
+    the least-remaining-work order.  Pure shortest-remaining-work-first
+    leaves the largest requests paused for as long as arrivals exceed the
+    capacity, so its p99 time-to-result grows past that of plain FIFO; with
+    the bound, requests past it are served in arrival order.
     ``max_active_cells`` optionally bounds the cells admitted at once.
     Backends with ``whole_requests`` true (one request at a time) get each
     request's remaining steps as one chunk."""
 
     def __init__(self, backend, chunk_ms: float = 8.0, depth: int = 3, clock=time.monotonic, sleep=time.sleep,
                  max_active_cells=None, est_gbs: float = 5500.0, max_chunk: int = 256, min_chunk: int = 4,
-                 policy: str = "fifo", target_cells: int = 8_000_000):
+                 policy: str = "fifo", target_cells: int = 8_000_000, max_wait_s=None):
         self.backend = backend
         self.chunk_ms = float(chunk_ms)
         self.depth = max(1, int(depth))
@@ -106,6 +112,7 @@ class Scheduler:
             raise ValueError(policy)
         self.policy = policy
         self.target_cells = int(target_cells)
+        self.max_wait_s = None if max_wait_s is None else float(max_wait_s)
 
     @staticmethod
     def _bpu(req):
@@ -119,11 +126,17 @@ class Scheduler:
         n = int(self.chunk_ms * 1e-3 / step_s)
         return max(self.min_chunk, min(self.max_chunk, n))
 
-    def _select(self, live):
+    def _select(self, live, now=0.0):
         """The requests that step in the next chunk."""
         if self.policy == "fifo" or getattr(self.backend, "whole_requests", False):
             return live
-        order = sorted(live, key=lambda a: a[2] * a[0].cells * self._bpu(a[0]))
+        late = self.max_wait_s
+
+        def key(a):
+            if late is not None and now - a[0].arrival_s > late:
+                return (0, a[0].arrival_s)
+            return (1, a[2] * a[0].cells * self._bpu(a[0]))
+        order = sorted(live, key=key)
         out, cells = [], 0
         for a in order:
             if out and cells >= self.target_cells:
@@ -166,7 +179,7 @@ class Scheduler:
                 cells += head.cells
             live = [a for a in active.values() if a[2] > 0]
             if live and issued - polled < self.depth:
-                run_now = self._select(live)
+                run_now = self._select(live, self.clock() - t0)
                 n = self._chunk(run_now)
                 if srpt:
                     quotas = {}

@@ -164,3 +164,31 @@ def test_srpt_runs_least_remaining_work_first():
     be2 = FakeBackend(capacity=10 ** 12, slots=8, clock=clk2)
     st2 = Scheduler(be2, clock=clk2, sleep=clk2.sleep, policy="fifo", max_chunk=64).run(reqs)
     assert {r.rid for r in st2.results} == {0, 1}
+
+
+def _overload(max_wait_s):
+    """One large request at t = 0 (50 chunks of 64 steps), then a small
+    request (4 chunks) every 20 ms for 2 s; one request runs per chunk
+    (target_cells = 1) and a chunk costs 6.4 ms, so the small requests alone
+    keep the backend busy."""
+    clk = VirtualClock()
+    be = FakeBackend(capacity=10 ** 12, slots=256, clock=clk)
+    reqs = [Req(0, 0.0, 10 ** 6, 64 * 50)]
+    reqs += [Req(i, 0.02 * i, 10 ** 3, 64 * 4) for i in range(1, 101)]
+    st = Scheduler(be, clock=clk, sleep=clk.sleep, policy="srpt", target_cells=1, max_chunk=64, min_chunk=64,
+                   max_wait_s=max_wait_s).run(reqs)
+    assert len(st.results) == 101 and not st.rejected
+    return {r.rid: r.finished for r in st.results}
+
+
+def test_srpt_max_wait_bounds_starvation():
+    """Pure shortest-remaining-work-first leaves the large request paused
+    until the stream of small ones ends; with max_wait_s it is granted once
+    it has waited that long, oldest first, and finishes well before."""
+    starve = _overload(None)
+    bounded = _overload(0.5)
+    last_small = max(t for rid, t in starve.items() if rid != 0)
+    assert starve[0] >= 0.9 * last_small
+    assert 0.5 < bounded[0] < 0.5 + 50 * 0.0064 + 0.05
+    # the small requests still all finish
+    assert all(bounded[i] > 0 for i in range(1, 101))
