@@ -79,7 +79,10 @@ __device__ __forceinline__ void update_cell(const SlotDev& sd, int parity, int c
     const S* A = static_cast<const S*>(sd.pop[parity]);
     S* B = static_cast<S*>(sd.pop[parity ^ 1]);
     M d[Q];
-    pull_cell<S>(A, sd.code, sd.p, x, y, z, cell, cc, d);
+    // mask-first bounce-back: served requests are small walled boxes, where a
+    // large share of the cells is next to a wall (72 instead of 56 registers,
+    // still faster on the seeded serving mix)
+    pull_cell<S, 0, FORM_AB, true>(A, sd.code, sd.p, x, y, z, cell, cc, d);
     relax_dev<M, FORCE>(d, sd.p);
 #pragma unroll
     for (int i = 0; i < Q; ++i) B[(int64_t)i * sd.p.ps + cell] = Storage<S>::store(d[i]);
