@@ -238,7 +238,7 @@ def test_autotune_keeps_state(storage, perm, tmp_path, monkeypatch):
     f0 = gpu.populations()
     v, b, ms = gpu.autotune(reps=3)
     assert np.array_equal(gpu.populations(), f0)
-    assert v in range(1, 16) and b % 32 == 0 and ms > 0
+    assert v in range(1, 18) and b % 32 == 0 and ms > 0
     assert (tmp_path / "tune.json").exists()
     again = Lattice(nx, ny, nz, 0.6, u_lid=(0.05, 0, 0), flags=flags, storage=storage)
     assert again.autotune(reps=3) == (v, b, ms)  # from the cache
