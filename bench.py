@@ -232,11 +232,10 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def ncu_traffic(profile_key: str, variant=None):
-    """Per-launch DRAM bytes (read + write) from the committed ncu figures,
-    if they were taken on the current kernel sources and for the kernel
-    variant being timed (profiles/traffic.json: per workload key, the source
-    hash and one figure per variant)."""
+def ncu_figure(profile_key: str, variant=None, field: str = "dram_bytes_per_launch"):
+    """A committed ncu figure (profiles/traffic.json: per workload key, the
+    source hash and one record per kernel variant), if it was taken on the
+    current kernel sources and for the kernel variant being timed."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as fh:
@@ -246,10 +245,39 @@ def ncu_traffic(profile_key: str, variant=None):
             per = rec.get("variants", {})
             hit = per.get(str(variant)) if variant is not None else None
             if hit:
-                return hit.get("dram_bytes_per_launch")
+                return hit.get(field)
     except (OSError, ValueError):
         pass
     return None
+
+
+def ncu_traffic(profile_key: str, variant=None):
+    """Per-launch DRAM bytes (read + write) from the committed ncu figures."""
+    return ncu_figure(profile_key, variant, "dram_bytes_per_launch")
+
+
+# FP64-pipe peak of a GB300 (the FP64 and Mixed2 forms are bound by it):
+# 2 FP64 thread instructions per SM per clock -- the nominal 1.25 TFLOP/s
+# FP64 (an FMA counting 2) over 152 SMs at 2.07 GHz, and what the ncu pipe
+# counters of the FP64 step kernel imply (one warp instruction per 16 clocks
+# per SM at 100 % pipe activity).
+FP64_PIPE_INST_PER_SM_CLK = 2
+GB300_SMS = 152
+GB300_MAX_SM_GHZ = 2.07
+
+
+def fp64_alu_roofline(storage, variant, glups):
+    """The ALU roofline of an FP64-arithmetic form: FP64-pipe thread
+    instructions per update (ncu, profiles/traffic.json) x updates per second
+    against the pipe's peak; None without a figure for this variant."""
+    per = ncu_figure(f"step_{storage}_tgv256", variant, "fp64_pipe_inst_per_update")
+    if not per:
+        return None
+    peak = GB300_SMS * FP64_PIPE_INST_PER_SM_CLK * GB300_MAX_SM_GHZ   # G inst / s
+    achieved = glups * per
+    return {"bound": "alu", "unit": "G FP64-pipe inst/s", "inst_per_update": per,
+            "achieved": round(achieved, 1), "peak": round(peak, 1), "frac": round(achieved / peak, 4),
+            "peak_kind": "derived: 152 SMs x 2 FP64 inst/clk x 2.07 GHz"}
 
 
 def tgv_inputs(n):
@@ -408,6 +436,8 @@ def forms_section(n, steps=200, device=None):
                     "glups": round(glups, 2), "gbs": round(gbs, 1),
                     "frac": round(gbs / peak, 4), "peak_kind": peak_kind,
                     "bytes_per_update": bytes_per_update(storage)})
+        if storage in ("f64", "f32d"):
+            out[-1]["alu"] = fp64_alu_roofline(storage, v, glups)
         lat.close()
         del lat
     return out
