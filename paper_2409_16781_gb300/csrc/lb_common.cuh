@@ -12,6 +12,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "lb_fpconv.cuh"
+
 namespace lbgb {
 
 constexpr int Q = 19;
@@ -91,8 +93,9 @@ struct f32d {
 template <> struct Storage<f32d> {
     using math = double;
     static constexpr int id = 4;
-    __device__ __forceinline__ static double load(f32d v) { return (double)v.v; }
-    __device__ __forceinline__ static f32d store(double v) { return f32d{__double2float_rn(v)}; }
+    // integer-pipe conversions (lb_fpconv.cuh): the FP64 pipe bounds this form
+    __device__ __forceinline__ static double load(f32d v) { return widen_f32(v.v); }
+    __device__ __forceinline__ static f32d store(double v) { return f32d{narrow_f64(v)}; }
 };
 
 // Parameters of one lattice as seen by the kernels.
