@@ -49,6 +49,19 @@ def bytes_required(nx, ny, nz, storage="f32", inplace=False) -> int:
     return int(L.lib().lb_bytes_required(int(nx), int(ny), int(nz), ctypes.byref(o)))
 
 
+def autotune_key(device_name, storage, dims, force, flags, trt_magic=0.0, inplace=False) -> str:
+    """The autotune cache key: GPU, storage, dims, forcing, geometry (a digest
+    of the flags, or "nowalls" when every cell is fluid), collision and
+    population layout -- everything the fastest step kernel depends on."""
+    import hashlib
+    fl = None if flags is None else np.ascontiguousarray(flags, dtype=np.uint8)
+    geo = ("walls:" + hashlib.blake2b(fl.tobytes(), digest_size=8).hexdigest()
+           if fl is not None and fl.any() else "nowalls")
+    nx, ny, nz = dims
+    return "|".join([str(device_name), str(storage), f"{nx}x{ny}x{nz}", "force" if force else "noforce", geo]
+                    + (["trt"] if trt_magic else []) + (["inplace"] if inplace else []))
+
+
 class Lattice:
     """A lattice advanced by liblbgb on one GPU.
 
@@ -213,15 +226,9 @@ class Lattice:
         best kernel depends on how many cells are next to a wall)
         (LBGB_AUTOTUNE_CACHE, default ~/.cache/lbgb/autotune.json).
         Returns (variant, block, ms/step)."""
-        import hashlib
-
         import torch
-        fl = self._flags
-        geo = ("walls:" + hashlib.blake2b(fl.tobytes(), digest_size=8).hexdigest()
-               if fl is not None and fl.any() else "nowalls")
-        key = "|".join([torch.cuda.get_device_name(self.device), str(self.storage),
-                        f"{self.nx}x{self.ny}x{self.nz}", "force" if self._force else "noforce", geo]
-                       + (["trt"] if self.trt_magic else []) + (["inplace"] if self.inplace else []))
+        key = autotune_key(torch.cuda.get_device_name(self.device), self.storage, (self.nx, self.ny, self.nz),
+                           self._force, self._flags, self.trt_magic, self.inplace)
         path = os.environ.get("LBGB_AUTOTUNE_CACHE",
                               os.path.join(os.path.expanduser("~"), ".cache", "lbgb", "autotune.json"))
         table = {}
