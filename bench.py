@@ -38,8 +38,8 @@ METRIC = "D3Q19 MLUPS & fraction of HBM roofline; batched-serve p50/p99 vs plain
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2, "f32d": 4}
 FALLBACK_HBM_GBS = 6800.0
 # the files that make up the step kernel (hashed to tie ncu figures to it)
-STEP_SOURCES = ("lb_common.cuh", "lb_fpconv.cuh", "lb_kernels.cuh", "lb_pairs.cuh", "lb_mbarrier.cuh", "lb_step.cu",
-                "lb_inplace.cu")
+STEP_SOURCES = ("lb_common.cuh", "lb_fpconv.cuh", "lb_internal.h", "lb_kernels.cuh", "lb_pairs.cuh", "lb_mbarrier.cuh",
+                "lb_step.cu", "lb_inplace.cu")
 
 
 def bytes_per_update(storage: str) -> int:

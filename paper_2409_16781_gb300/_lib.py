@@ -114,6 +114,17 @@ def lib():
     return _lib
 
 
+def load(path: str):
+    """Another build of the library (the bounds-checked test build), with the
+    same signatures; loaded RTLD_LOCAL beside liblbgb.so."""
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
 def check(status: int, what: str = "") -> int:
     if status == LB_OK:
         return status

@@ -48,15 +48,28 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(PKG, "liblbgb_checked.so")
+
+
+def build_checked(verbose: bool = False, force: bool = False) -> str:
+    """The bounds-checked test build (-DLBGB_CHECKED, liblbgb_checked.so):
+    every population load and store of the step kernels is checked against
+    its launch's arrays and counted, not performed, when outside.  Used by
+    tests only; the product loads liblbgb.so."""
+    return build(verbose, force, ["-DLBGB_CHECKED"], BUILD_CHECKED, LIB_CHECKED)
+
+
+def build(verbose: bool = False, force: bool = False, extra_flags=None, build_dir: str = BUILD,
+          lib_path: str = LIB) -> str:
+    os.makedirs(build_dir, exist_ok=True)
     nv = nvcc()
     hdrs = _headers()
     flags = NVCC_FLAGS + list(extra_flags or [])
     jobs = []
     objs = []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + hdrs):
             jobs.append([nv] + ARCH + flags + ["-c", src, "-o", obj])
@@ -72,11 +85,11 @@ def build(verbose: bool = False, force: bool = False, extra_flags=None) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
         list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib_path, objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         run([nv] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

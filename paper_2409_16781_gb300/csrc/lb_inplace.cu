@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(128, 8) step_kernel_inplace_pairs(const S* Ar,
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             float a, b;
-            split2<S>(*reinterpret_cast<const V*>(Ar + (int64_t)i * p.ps + cell0), a, b);
+            split2<S>(ld_pop<0>(reinterpret_cast<const V*>(Ar + (int64_t)i * p.ps + cell0)), a, b);
             d[i] = f32x2(a, b);
         }
     } else {
@@ -90,16 +90,16 @@ __global__ void __launch_bounds__(128, 8) step_kernel_inplace_pairs(const S* Ar,
         for (int i = 0; i < Q; ++i) {
             const S* rowp = Ar + (int64_t)D3Q19::opp(i) * p.ps + yo[D3Q19::cy(i) + 1] + zo[D3Q19::cz(i) + 1];
             float a, b;
-            split2<S>(*reinterpret_cast<const V*>(rowp + x0), a, b);
+            split2<S>(ld_pop<0>(reinterpret_cast<const V*>(rowp + x0)), a, b);
             if (D3Q19::cx(i) == 0) {
                 d[i] = f32x2(a, b);
             } else if (D3Q19::cx(i) == 1) {  // source x - 1
                 float prev = __shfl_up_sync(0xffffffffu, b, 1);
-                if (own_prev && active) prev = Storage<S>::load(rowp[x0 == 0 ? nx - 1 : x0 - 1]);
+                if (own_prev && active) prev = Storage<S>::load(ld_pop<0>(rowp + (x0 == 0 ? nx - 1 : x0 - 1)));
                 d[i] = f32x2(prev, a);
             } else {  // source x + 1
                 float next = __shfl_down_sync(0xffffffffu, a, 1);
-                if (own_next && active) next = Storage<S>::load(rowp[x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2]);
+                if (own_next && active) next = Storage<S>::load(ld_pop<0>(rowp + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2)));
                 d[i] = f32x2(b, next);
             }
         }
@@ -116,10 +116,10 @@ __global__ void __launch_bounds__(128, 8) step_kernel_inplace_pairs(const S* Ar,
         for (int i = 0; i < Q; ++i) {
             S* q = Aw + (int64_t)D3Q19::opp(i) * p.ps + cell0;
             if (f0 && f1) {
-                *reinterpret_cast<V*>(q) = pack2<S>(d[i].v.x, d[i].v.y);
+                st_pop<0>(reinterpret_cast<V*>(q), pack2<S>(d[i].v.x, d[i].v.y));
             } else {
-                if (f0) q[0] = Storage<S>::store(d[i].v.x);
-                if (f1) q[1] = Storage<S>::store(d[i].v.y);
+                if (f0) st_pop<0>(q, Storage<S>::store(d[i].v.x));
+                if (f1) st_pop<0>(q + 1, Storage<S>::store(d[i].v.y));
             }
         }
     } else {
@@ -131,17 +131,17 @@ __global__ void __launch_bounds__(128, 8) step_kernel_inplace_pairs(const S* Ar,
             S* rowt = Aw + (int64_t)i * p.ps + yt[D3Q19::cy(i) + 1] + zt[D3Q19::cz(i) + 1];
             if (D3Q19::cx(i) == 0) {
                 if (f0 && f1) {
-                    *reinterpret_cast<V*>(rowt + x0) = pack2<S>(d[i].v.x, d[i].v.y);
+                    st_pop<0>(reinterpret_cast<V*>(rowt + x0), pack2<S>(d[i].v.x, d[i].v.y));
                 } else {
-                    if (f0) rowt[x0] = Storage<S>::store(d[i].v.x);
-                    if (f1) rowt[x0 + 1] = Storage<S>::store(d[i].v.y);
+                    if (f0) st_pop<0>(rowt + x0, Storage<S>::store(d[i].v.x));
+                    if (f1) st_pop<0>(rowt + x0 + 1, Storage<S>::store(d[i].v.y));
                 }
             } else if (D3Q19::cx(i) == 1) {  // targets x0 + 1, x0 + 2
-                if (f0) rowt[x0 + 1] = Storage<S>::store(d[i].v.x);
-                if (f1) rowt[x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2] = Storage<S>::store(d[i].v.y);
+                if (f0) st_pop<0>(rowt + x0 + 1, Storage<S>::store(d[i].v.x));
+                if (f1) st_pop<0>(rowt + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2), Storage<S>::store(d[i].v.y));
             } else {  // targets x0 - 1, x0
-                if (f0) rowt[x0 == 0 ? nx - 1 : x0 - 1] = Storage<S>::store(d[i].v.x);
-                if (f1) rowt[x0] = Storage<S>::store(d[i].v.y);
+                if (f0) st_pop<0>(rowt + (x0 == 0 ? nx - 1 : x0 - 1), Storage<S>::store(d[i].v.x));
+                if (f1) st_pop<0>(rowt + x0, Storage<S>::store(d[i].v.y));
             }
         }
     }
@@ -203,8 +203,16 @@ static cudaError_t step_inplace_t(int variant, void* A, const uint8_t* code, con
     return cudaErrorInvalidValue;
 }
 
+#ifdef LBGB_CHECKED
+LBGB_CHECKED_UNIT(lbgb_checked_violations_inplace)
+#endif
+
 cudaError_t launch_step_inplace(int storage, int variant, void* A, const uint8_t* code, const LatticeParams& p,
                                 int form, int block, cudaStream_t st) {
+#ifdef LBGB_CHECKED
+    const cudaError_t ce = check_window_set(A, A, p, storage, st);
+    if (ce != cudaSuccess) return ce;
+#endif
     LBGB_DISPATCH(storage, step_inplace_t<S>(variant, A, code, p, form, block, st));
 }
 

@@ -33,6 +33,37 @@ cudaError_t launch_step_inplace(int storage, int variant, void* A, const uint8_t
                                 int form, int block, cudaStream_t st);
 
 // Instantiate CALL with S = the storage type of `storage` and return it.
+#ifdef LBGB_CHECKED
+// Bounds-checked build: each launching translation unit sets its own
+// windows (see CheckWindow in lb_kernels.cuh) before every step launch and
+// reports the accesses that fell outside them.
+#define LBGB_CHECKED_UNIT(NAME)                                                                          \
+    static cudaError_t check_window_set(const void* A, const void* B, const LatticeParams& p, int storage, \
+                                        cudaStream_t st) {                                             \
+        CheckWindow w;                                                                                 \
+        const uintptr_t plane = (uintptr_t)Q * (uintptr_t)p.ps * (uintptr_t)storage_bytes(storage);    \
+        w.rlo = reinterpret_cast<uintptr_t>(A);                                                        \
+        w.rhi = w.rlo + plane;                                                                         \
+        w.wlo = reinterpret_cast<uintptr_t>(B);                                                        \
+        w.whi = w.wlo + plane;                                                                         \
+        w.on = 1;                                                                                      \
+        return cudaMemcpyToSymbolAsync(g_check, &w, sizeof w, 0, cudaMemcpyHostToDevice, st);         \
+    }                                                                                                  \
+    extern "C" unsigned long long NAME(int reset, unsigned long long* checks) {                        \
+        unsigned long long v = 0, c = 0;                                                               \
+        if (cudaDeviceSynchronize() != cudaSuccess) return ~0ull;                                      \
+        if (cudaMemcpyFromSymbol(&v, g_violations, sizeof v) != cudaSuccess) return ~0ull;             \
+        if (cudaMemcpyFromSymbol(&c, g_checks, sizeof c) != cudaSuccess) return ~0ull;                 \
+        if (checks) *checks = c;                                                                       \
+        if (reset) {                                                                                   \
+            const unsigned long long z = 0;                                                            \
+            if (cudaMemcpyToSymbol(g_violations, &z, sizeof z) != cudaSuccess) return ~0ull;           \
+            if (cudaMemcpyToSymbol(g_checks, &z, sizeof z) != cudaSuccess) return ~0ull;               \
+        }                                                                                              \
+        return v;                                                                                      \
+    }
+#endif
+
 #define LBGB_DISPATCH(storage, CALL)                      \
     switch (storage) {                                    \
         case 0: { using S = double; return CALL; }        \

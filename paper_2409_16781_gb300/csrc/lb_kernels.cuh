@@ -14,6 +14,25 @@
 
 namespace lbgb {
 
+#ifdef LBGB_CHECKED
+// Bounds-checked build (a test build, liblbgb_checked.so, never the
+// product): every population load and store of the step kernels goes through
+// ld_pop / st_pop, which check it against the current launch's windows --
+// loads inside the array the step reads, stores inside the array it writes
+// (19 planes of ps values each) -- set on the launch's stream by the
+// launching translation unit (check_window_set).  An access outside is
+// counted in g_violations and skipped (a load returns 0), so a bad index
+// neither faults nor corrupts memory.  Per translation unit; zero (off) in
+// the units that launch no step kernel.
+struct CheckWindow {
+    uintptr_t rlo, rhi, wlo, whi;
+    int on;
+};
+static __constant__ CheckWindow g_check;
+static __device__ unsigned long long g_violations;
+static __device__ unsigned long long g_checks;  // accesses checked (shows the checks ran)
+#endif
+
 // Global loads/stores of population values with a cache policy:
 //   HINT 0: default (L1 + L2),  1: streaming (.cs, evict-first),
 //   HINT 2: L2 only for loads (.cg), streaming stores.
@@ -22,6 +41,16 @@ __device__ __forceinline__ S ld_pop(const S* p) {
     if constexpr (std::is_same<S, f32d>::value) {
         return f32d{ld_pop<HINT>(reinterpret_cast<const float*>(p))};
     } else {
+#ifdef LBGB_CHECKED
+        if (g_check.on) {
+            const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+            atomicAdd(&g_checks, 1ull);
+            if (a < g_check.rlo || a + sizeof(S) > g_check.rhi) {
+                atomicAdd(&g_violations, 1ull);
+                return S{};
+            }
+        }
+#endif
         if constexpr (HINT == 1) return __ldcs(p);
         else if constexpr (HINT == 2) return __ldcg(p);
         else return *p;
@@ -32,6 +61,16 @@ __device__ __forceinline__ void st_pop(S* p, S v) {
     if constexpr (std::is_same<S, f32d>::value) {
         st_pop<HINT>(reinterpret_cast<float*>(p), v.v);
     } else {
+#ifdef LBGB_CHECKED
+        if (g_check.on) {
+            const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+            atomicAdd(&g_checks, 1ull);
+            if (a < g_check.wlo || a + sizeof(S) > g_check.whi) {
+                atomicAdd(&g_violations, 1ull);
+                return;
+            }
+        }
+#endif
         if constexpr (HINT == 0) *p = v;
         else __stcs(p, v);
     }
@@ -480,7 +519,7 @@ __device__ __forceinline__ void inplace_update(const S* Ar, S* Aw, const uint8_t
     relax_dev<M, FORCE>(d, p);
     if constexpr (FORM == FORM_STREAMED) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) Aw[(int64_t)D3Q19::opp(i) * p.ps + cell] = Storage<S>::store(d[i]);
+        for (int i = 0; i < Q; ++i) st_pop<0>(Aw + (int64_t)D3Q19::opp(i) * p.ps + cell, Storage<S>::store(d[i]));
     } else {
         const int nx = p.nx, ny = p.ny, nz = p.nz;
         const int nxy = nx * ny;
@@ -490,7 +529,7 @@ __device__ __forceinline__ void inplace_update(const S* Ar, S* Aw, const uint8_t
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int t = xt[D3Q19::cx(i) + 1] + yt[D3Q19::cy(i) + 1] + zt[D3Q19::cz(i) + 1];
-            Aw[(int64_t)i * p.ps + t] = Storage<S>::store(d[i]);
+            st_pop<0>(Aw + (int64_t)i * p.ps + t, Storage<S>::store(d[i]));
         }
     }
 }

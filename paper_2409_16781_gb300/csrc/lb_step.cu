@@ -739,7 +739,7 @@ __global__ void __launch_bounds__(tma_threads(G), G == 4 ? 2 : (G == 2 ? 4 : 3))
         const uint32_t solid_mask = G == 4 ? 0x03030303u : (G == 2 ? 0x0303u : 0x03u);
         if ((codes & solid_mask) == 0) {
 #pragma unroll
-            for (int i = 0; i < Q; ++i) *reinterpret_cast<W*>(B16 + (int64_t)i * p.ps + cell0) = out[i];
+            for (int i = 0; i < Q; ++i) st_pop<0>(reinterpret_cast<W*>(B16 + (int64_t)i * p.ps + cell0), out[i]);
         } else {  // solid cells are never written
 #pragma unroll
             for (int kk = 0; kk < G; ++kk) {
@@ -749,7 +749,7 @@ __global__ void __launch_bounds__(tma_threads(G), G == 4 ? 2 : (G == 2 ? 4 : 3))
                     uint32_t word;
                     if constexpr (G == 4) word = kk < 2 ? out[i].x : out[i].y;
                     else word = out[i];
-                    B16[(int64_t)i * p.ps + cell0 + kk] = (uint16_t)(word >> (16 * (kk & 1)));
+                    st_pop<0>(B16 + (int64_t)i * p.ps + cell0 + kk, (uint16_t)(word >> (16 * (kk & 1))));
                 }
             }
         }
@@ -923,8 +923,16 @@ static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* co
     }
 }
 
+#ifdef LBGB_CHECKED
+LBGB_CHECKED_UNIT(lbgb_checked_violations_step)
+#endif
+
 cudaError_t launch_step(int storage, int variant, const void* A, void* B, const uint8_t* code,
                         const LatticeParams& p, int block, cudaStream_t st) {
+#ifdef LBGB_CHECKED
+    const cudaError_t ce = check_window_set(A, B, p, storage, st);
+    if (ce != cudaSuccess) return ce;
+#endif
     LBGB_DISPATCH(storage, step_t<S>(variant, A, B, code, p, block, st));
 }
 
