@@ -84,6 +84,8 @@ def parse_args(argv=None):
                     help="arrival rates of --workload serve, as multiples of the sequential FP32 capacity")
     ap.add_argument("--serve-max-wait", type=float, default=60.0,
                     help="seconds after which a waiting request is served oldest-first (0 = no bound)")
+    ap.add_argument("--serve-log", default=None,
+                    help="path prefix for per-request JSON-lines records of the serving runs")
     ap.add_argument("--serve-tight-gb", type=float, default=0.75,
                     help="HBM budget of the memory-bound serving comparison (two arrays vs in place; 0 = skip)")
     return ap.parse_args(argv)
@@ -446,7 +448,7 @@ def forms_section(n, steps=200, device=None):
 
 # ---------------------------------------------------------------- serving
 def run_serving(n_requests, rate_multipliers=(2.0,), budget_gb=64.0, seed=16781, calib=16,
-                device=None, tight_budget_gb=0.75, max_wait_s=60.0):
+                device=None, tight_budget_gb=0.75, max_wait_s=60.0, log_prefix=None):
     """Continuous-batching serving of a seeded Poisson stream of cavity /
     channel requests (sizes log-uniform 16^3..192^3, aspect <= 4, tau in
     [0.52, 1], steps in [200, 5000], FP32 / shifted-FP16 50/50), against the
@@ -480,6 +482,9 @@ def run_serving(n_requests, rate_multipliers=(2.0,), budget_gb=64.0, seed=16781,
         torch.cuda.synchronize()
         ss = serve(reqs, SequentialBackend("f32", device=device))
         torch.cuda.synchronize()
+        if log_prefix:   # one JSON line per request (serve.ServeStats.records)
+            sb.write_jsonl(f"{log_prefix}_{mult:g}x_batched.jsonl")
+            ss.write_jsonl(f"{log_prefix}_{mult:g}x_sequential.jsonl")
         out["runs"].append({"rate_multiplier": mult, "rate_hz": round(mult * capacity, 3),
                             "batched": sb.summary(), "sequential_fp32": ss.summary()})
     if tight_budget_gb:
@@ -858,7 +863,7 @@ def serve_line(args):
     n = args.serve_requests if args.serve_requests else 2000
     rates = tuple(float(r) for r in args.serve_rates.split(","))
     sv = run_serving(n, rates, args.serve_budget_gb, tight_budget_gb=args.serve_tight_gb,
-                     max_wait_s=args.serve_max_wait or None)
+                     max_wait_s=args.serve_max_wait or None, log_prefix=args.serve_log)
     hi = sv["runs"][-1]
     return {"metric": METRIC, "value": hi["batched"]["mlups"], "unit": "MLUPS", "n_gpus": 1,
             "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak",

@@ -165,6 +165,13 @@ class Lattice:
         L.check(self.lib.lb_moments(self._h, _dptr(rho), _dptr(u)), "lb_moments")
         return rho, u
 
+    def write_vtk(self, path: str, title: str = "lbgb fields"):
+        """rho, u (lb_moments) and the flags as a legacy VTK file (vtk.write_vtk)."""
+        from .vtk import write_vtk
+        rho, u = self.moments()
+        flags = None if self._flags is None else self._flags.reshape(self.shape)
+        write_vtk(path, rho, u, flags, title=title)
+
     def moments_device(self, rho=None, u=None):
         """(rho, u) as float64 CUDA tensors, issued on the lattice's stream."""
         import torch

@@ -54,6 +54,27 @@ class ServeStats:
     makespan: float = 0.0
     launches: int = 0
 
+    def records(self):
+        """One dict per finished request (times in seconds from the start of
+        the run on the host's monotonic clock)."""
+        for r in sorted(self.results, key=lambda r: r.rid):
+            yield {"rid": r.rid, "arrival_s": round(r.arrival, 6), "admitted_s": round(r.admitted, 6),
+                   "finished_s": round(r.finished, 6), "latency_s": round(r.latency, 6), "cells": r.cells,
+                   "steps": r.steps, "storage": r.storage}
+        for q in self.rejected:
+            yield {"rid": q.rid, "arrival_s": round(q.arrival_s, 6), "rejected": True,
+                   "cells": q.cells, "steps": q.steps, "storage": getattr(q, "storage", "f32")}
+
+    def write_jsonl(self, path: str) -> int:
+        """Write records() as JSON lines; returns the number written."""
+        import json
+        n = 0
+        with open(path, "w") as fh:
+            for rec in self.records():
+                fh.write(json.dumps(rec) + "\n")
+                n += 1
+        return n
+
     def summary(self) -> dict:
         lat = np.array([r.latency for r in self.results]) if self.results else np.zeros(1)
         lups = float(sum(r.cells * r.steps for r in self.results))

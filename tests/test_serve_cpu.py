@@ -192,3 +192,27 @@ def test_srpt_max_wait_bounds_starvation():
     assert 0.5 < bounded[0] < 0.5 + 50 * 0.0064 + 0.05
     # the small requests still all finish
     assert all(bounded[i] > 0 for i in range(1, 101))
+
+
+def test_per_request_jsonl_records(tmp_path):
+    """Every finished and every rejected request gets one JSON line; the
+    latency is finished - arrival and the p50 of the lines matches the
+    summary's."""
+    import json
+
+    import numpy as np
+    clk = VirtualClock()
+    be = FakeBackend(capacity=20000, slots=4, clock=clk)   # the last request never fits
+    reqs = [Req(i, 0.01 * i, 10 + 5 * i, 8 + i) for i in range(12)] + [Req(99, 0.2, 10 ** 6, 4)]
+    st = Scheduler(be, clock=clk, sleep=clk.sleep, max_chunk=8).run(reqs)
+    path = tmp_path / "serve.jsonl"
+    n = st.write_jsonl(str(path))
+    lines = [json.loads(l) for l in path.read_text().splitlines()]
+    assert n == len(lines) == 13
+    done = [l for l in lines if not l.get("rejected")]
+    assert len(done) == 12 and [l["rid"] for l in done] == list(range(12))
+    assert [l["rid"] for l in lines if l.get("rejected")] == [99]
+    for l in done:
+        assert abs(l["latency_s"] - (l["finished_s"] - l["arrival_s"])) < 1e-5
+        assert l["arrival_s"] <= l["admitted_s"] <= l["finished_s"]
+    assert abs(np.percentile([l["latency_s"] for l in done], 50) - st.summary()["p50_s"]) < 1e-3
