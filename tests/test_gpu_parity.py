@@ -335,3 +335,18 @@ def test_flow_past_cylinder(storage, perm):
     for trt in (0.0, 3 / 16):
         ora, gpu = run_pair(nx, ny, nz, 0.56, 400, storage, flags, (0.05, 0, 0), trt_magic=trt)
         check_pair(ora, gpu, storage, perm, flags)
+
+
+def test_write_vtk_matches_moments(tmp_path):
+    """Lattice.write_vtk writes what lb_moments returns, and the flags."""
+    from paper_2409_16781_gb300.vtk import read_vtk
+    flags = W.cavity_flags(10, 8, 6)
+    gpu = Lattice(10, 8, 6, 0.6, u_lid=(0.1, 0, 0), flags=flags, storage="f32")
+    gpu.step(20)
+    rho, u = gpu.moments()
+    path = tmp_path / "cavity.vtk"
+    gpu.write_vtk(str(path))
+    r = read_vtk(str(path))
+    assert r["dims"] == (10, 8, 6)
+    assert np.array_equal(r["rho"], rho) and np.array_equal(r["u"], u) and np.array_equal(r["flags"], flags)
+    gpu.close()
