@@ -214,14 +214,40 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- helpers
+def strip_comments(src: str) -> str:
+    """C/C++ source without its comments and with runs of blank space
+    collapsed (string and character literals kept verbatim): the code the
+    compiler sees, so that editing a comment does not change the hash."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_hash() -> str:
-    """Hash of the CUDA sources; a committed ncu traffic figure is only
-    reported while it matches the kernels being timed."""
+    """Hash of the step kernels' CUDA code (comments excluded); a committed
+    ncu figure is only reported while it matches the kernels being timed."""
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2409_16781_gb300", "csrc")
     for name in STEP_SOURCES:
-        with open(os.path.join(cs, name), "rb") as fh:
-            h.update(name.encode() + b"\0" + fh.read())
+        with open(os.path.join(cs, name), encoding="utf-8") as fh:
+            h.update(name.encode() + b"\0" + strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -12,7 +12,11 @@
 // contiguous 32-element run (the y/z-shifted directions are row-aligned, the
 // x-shifted ones are offset by one element and pick up one extra sector,
 // served from L1/L2).  Interior cells read only their own code byte; cells
-// next to a wall read the 18 neighbour codes (cached) for bounce-back.
+// next to a wall read the 18 neighbour codes (cached) for bounce-back --
+// variants 16 and 17 read all 18 before any value (MASK_FIRST), so that the
+// value loads of such a cell are in flight together.  The other launch
+// shapes (two or four cells per thread, packed FP32 pairs, a TMA pipeline)
+// are documented at their kernels below; lb_set_kernel numbers them.
 #include <type_traits>
 
 #include "lb_internal.h"

@@ -76,3 +76,17 @@ def test_serving_defaults():
     assert a.serve_requests is None and a.serve_max_wait == 60.0 and a.serve_tight_gb == 0.75
     a = bench.parse_args(["--workload", "serve", "--serve-rates", "2", "--serve-max-wait", "0"])
     assert a.serve_rates == "2" and not a.serve_max_wait
+
+
+def test_source_hash_ignores_comments_only():
+    """The hash behind the committed ncu figures covers code, not comments:
+    editing a comment keeps it, changing a token changes it, and comment
+    markers inside string or character literals are code."""
+    s = bench.strip_comments
+    code = 'int a = 1; // the cell\'s "own" value\n/* block\n comment */ int b = 2;'
+    assert s(code) == "int a = 1; int b = 2;"
+    assert s(code.replace("the cell's", "a cell's")) == s(code)
+    assert s(code.replace("b = 2", "b = 3")) != s(code)
+    assert s('const char* p = "// not a comment"; char q = \'/\';') == \
+        'const char* p = "// not a comment"; char q = \'/\';'
+    assert s('x = "a\\"b // c"; y;') == 'x = "a\\"b // c"; y;'
