@@ -251,6 +251,9 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e, nominal
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -399,7 +402,9 @@ def run_ours(args, dist: Dist):
             "traffic": ncu_traffic(f"step_{args.storage}_tgv{n}" + ("_inplace" if args.inplace else ""),
                                    tuned[0] if tuned else args.kernel),
             "algorithmic_bytes_per_launch": bpu * N, "kernel": "lb step kernel",
-            "kernel_ms_mean": round(kernel_ms, 5), "kernel_ms_median": round(statistics.median(step_ms), 5)}
+            "kernel_ms_mean": round(kernel_ms, 5), "kernel_ms_median": round(statistics.median(step_ms), 5),
+            # the same figure against the nominal HBM3e bandwidth, for context
+            "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4), "nominal_peak": NOMINAL_HBM_GBS}
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": dist.world,
