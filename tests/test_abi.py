@@ -140,3 +140,43 @@ def test_selftest_wait_rejects_bad_deadlines(lib):
     """lb_selftest_wait validates its deadline before any device work."""
     for bad in (0.0, -1.0, 6.0, float("nan")):
         assert lib.lb_selftest_wait(bad, None) == L.LB_EINVAL
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include "lbgb.h"
+int main(void) {
+    lb_options o;
+    lb_default_options(&o);
+    o.storage = LB_F32;
+    size_t two = lb_bytes_required(64, 32, 16, &o);
+    o.inplace = 1;
+    size_t one = lb_bytes_required(64, 32, 16, &o);
+    int c[57];
+    double w[19];
+    lb_velocity_set(c, w);
+    printf("%zu %zu %d %d %d %.17g %s\n", two, one, c[3], c[4], c[5], w[0], lb_status_string(LB_EINVAL));
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_links(lib, tmp_path):
+    """include/lbgb.h compiles as strict C99 with warnings as errors, and a C
+    program links liblbgb.so and calls its host-only entry points."""
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "t.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "t"
+    libdir = os.path.dirname(L.LIB_PATH)
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-L", libdir, "-llbgb", f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    two, one = int(out[0]), int(out[1])
+    assert two - one == 19 * 64 * 32 * 16 * 4       # one population array fewer in place
+    assert out[2:5] == ["1", "0", "0"]               # c_1 = (+1, 0, 0)
+    assert float(out[5]) == 1 / 3
+    assert " ".join(out[6:]) == "invalid argument"
