@@ -21,6 +21,7 @@
 #include "lbgb.h"
 #include "lb_internal.h"
 #include "lb_kernels.cuh"
+#include "lb_pool.h"
 
 namespace lbgb {
 namespace {
@@ -180,55 +181,6 @@ int bfail(int status, const char* fmt, ...) {
 int bcuda(cudaError_t e, const char* what) { return bfail(LB_ECUDA, "%s: %s", what, cudaGetErrorString(e)); }
 inline size_t rup(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// First-fit allocator over [0, size) with coalescing, in BALIGN units.
-class Pool {
-   public:
-    void reset(size_t size) {
-        free_.clear();
-        if (size) free_[0] = size;
-        size_ = size;
-    }
-    bool alloc(size_t bytes, size_t* off) {
-        bytes = rup(bytes, BALIGN);
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= bytes) {
-                *off = it->first;
-                const size_t rest = it->second - bytes;
-                const size_t start = it->first + bytes;
-                free_.erase(it);
-                if (rest) free_[start] = rest;
-                return true;
-            }
-        }
-        return false;
-    }
-    void release(size_t off, size_t bytes) {
-        bytes = rup(bytes, BALIGN);
-        auto it = free_.emplace(off, bytes).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-    size_t free_bytes() const {
-        size_t s = 0;
-        for (auto& kv : free_) s += kv.second;
-        return s;
-    }
-
-   private:
-    std::map<size_t, size_t> free_;
-    size_t size_ = 0;
-};
-
 // Kernel type of a slot: its storage, plus BATCH_STORAGES if it is in place.
 inline int kernel_type(int storage, int inplace) { return storage + (inplace ? BATCH_STORAGES : 0); }
 
@@ -304,7 +256,7 @@ struct lb_batch {
     size_t staging_bytes = 0;
     char* pool_base = nullptr;
     size_t pool_bytes = 0;
-    Pool pool;
+    Pool<BALIGN> pool;  // slot placement in the pool buffer (lb_pool.h)
     std::vector<SlotHost> slots;
     // host view of each slot's counters: the latest snapshot applied
     std::vector<int64_t> last_rem;
