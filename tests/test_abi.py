@@ -180,3 +180,25 @@ def test_header_is_plain_c_and_links(lib, tmp_path):
     assert out[2:5] == ["1", "0", "0"]               # c_1 = (+1, 0, 0)
     assert float(out[5]) == 1 / 3
     assert " ".join(out[6:]) == "invalid argument"
+
+
+def test_batch_sizes(lib):
+    """Slot sizes: 19 planes of round_up(N, 128) values per population
+    array plus N code bytes, each rounded to 256 bytes; in place one array
+    fewer; bad arguments give 0.  The fixed area grows with max_slots and
+    holds at least the 16 MiB staging area."""
+    def rup(v, a):
+        return (v + a - 1) // a * a
+    sizes = {L.LB_F64: 8, L.LB_F32: 4, L.LB_F16S: 2, L.LB_BF16S: 2, L.LB_F32D: 4}
+    for (nx, ny, nz) in ((16, 16, 16), (33, 5, 7), (1, 1, 1), (192, 96, 64)):
+        n = nx * ny * nz
+        ps = rup(n, 128)
+        for st, sb in sizes.items():
+            pops = rup(19 * ps * sb, 256)
+            assert lib.lb_batch_slot_bytes(nx, ny, nz, st, 0) == 2 * pops + rup(n, 256)
+            assert lib.lb_batch_slot_bytes(nx, ny, nz, st, 1) == pops + rup(n, 256)
+    for bad in ((0, 4, 4, L.LB_F32, 0), (4, 4, 4, 9, 0), (4, 4, 4, L.LB_F32, 2), (2048, 2048, 512, L.LB_F32, 0)):
+        assert lib.lb_batch_slot_bytes(*bad) == 0
+    f1, f1k = lib.lb_batch_fixed_bytes(1), lib.lb_batch_fixed_bytes(1024)
+    assert f1 >= 16 << 20 and f1k > f1
+    assert lib.lb_batch_fixed_bytes(0) == 0 and lib.lb_batch_fixed_bytes(65537) == 0
