@@ -117,8 +117,8 @@ int lb_velocity_set(int *c, double *w);
  * codes, host-transfer staging and reduction scratch).  0 on bad sizes. */
 size_t lb_bytes_required(int nx, int ny, int nz, const lb_options *opt);
 
-/* Create a lattice (Sec. 3.3 use cases; lb_create(nx,ny,nz,tau,u_lid,flags)
- * of the problem statement).
+/* Create a lattice of nx x ny x nz cells for one of the use cases of
+ * Sec. 3.3 (lid-driven cavity, Taylor-Green vortex, flow past an obstacle).
  *   tau    BGK relaxation time, omega = 1/tau of Eq. 1; must be > 1/2.
  *   u_lid  velocity of LB_LID cells and of the free stream of LB_FARFIELD
  *          cells (NULL = 0); halfway bounce-back off a LID source adds

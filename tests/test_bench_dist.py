@@ -1,6 +1,6 @@
 """Multi-process bookkeeping of bench.py on CPU (gloo, world size 2).
 
-The lattice update does not shard in this build (replicas only): every rank
+The lattice update does not shard here (replicas only): every rank
 advances its own lattice and only the timing is reduced.  These tests run the
 same Dist / aggregate_replicas code the GPU bench uses, with gloo ranks.
 """
