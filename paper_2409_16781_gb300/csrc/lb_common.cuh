@@ -11,6 +11,7 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <type_traits>
 
 #include "lb_fpconv.cuh"
 
@@ -109,7 +110,20 @@ struct LatticeParams {
     double ulid[3];   // lid velocity (and free-stream velocity of far-field cells)
     double ff[19];    // far-field deviations f^eq_i(1, ulid) - w_i (set_farfield)
     int* err;         // device error word (bounded waits that gave up), or nullptr
+    // omega, omega_m and g rounded to FP32 on the host (set_farfield): the
+    // FP32-arithmetic kernels read these instead of converting the FP64
+    // fields in every thread (a GB300 runs that conversion on its narrow
+    // FP64 pipe); the rounding is the same, so the results are too.
+    float omega_f, omega_m_f, g_f[3];
 };
+
+// A lattice parameter in the arithmetic type M: the FP64 field for FP64
+// arithmetic, its FP32 copy otherwise.
+template <class M>
+__host__ __device__ __forceinline__ M param(double d, float f) {
+    if constexpr (sizeof(M) == sizeof(double) && !std::is_class<M>::value) return (M)d;
+    else return M(f);
+}
 
 // The free stream seen from a far-field cell (the inflow and outflow planes
 // of flow past an obstacle, the paper's von Karman street use case,
@@ -117,6 +131,9 @@ struct LatticeParams {
 // 3/2 U.U) of the equilibrium of Eq. 2-3 at density 1 and U = ulid, filled
 // on the host once per lattice so that kernels only read them.
 inline void set_farfield(LatticeParams& p) {
+    p.omega_f = (float)p.omega;
+    p.omega_m_f = (float)p.omega_m;
+    for (int a = 0; a < 3; ++a) p.g_f[a] = (float)p.g[a];
     const double uu = p.ulid[0] * p.ulid[0] + p.ulid[1] * p.ulid[1] + p.ulid[2] * p.ulid[2];
     for (int i = 0; i < 19; ++i) {
         const double cu = D3Q19::cx(i) * p.ulid[0] + D3Q19::cy(i) * p.ulid[1] + D3Q19::cz(i) * p.ulid[2];

@@ -341,9 +341,9 @@ __device__ __forceinline__ void macro_dev(const M (&d)[Q], const LatticeParams& 
     moment_sums<M>(d, drho, jx, jy, jz);
     rho = M(1) + drho;
     const M inv = recip(rho);
-    ux = fmad(jx, inv, M(0.5) * (M)p.g[0]);
-    uy = fmad(jy, inv, M(0.5) * (M)p.g[1]);
-    uz = fmad(jz, inv, M(0.5) * (M)p.g[2]);
+    ux = fmad(jx, inv, M(0.5) * param<M>(p.g[0], p.g_f[0]));
+    uy = fmad(jy, inv, M(0.5) * param<M>(p.g[1], p.g_f[1]));
+    uz = fmad(jz, inv, M(0.5) * param<M>(p.g[2], p.g_f[2]));
 }
 
 // BGK relaxation towards f^eq (Eq. 2-3) plus the Guo source term (the S_i
@@ -394,17 +394,17 @@ __device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams&
     }
     const M rho = M(1) + drho;
     const M inv = recip(rho);
-    const M ux = fmad(jx, inv, M(0.5) * (M)p.g[0]);
-    const M uy = fmad(jy, inv, M(0.5) * (M)p.g[1]);
-    const M uz = fmad(jz, inv, M(0.5) * (M)p.g[2]);
-    const M om = (M)p.omega;
-    const M omm = (M)p.omega_m;
+    const M ux = fmad(jx, inv, M(0.5) * param<M>(p.g[0], p.g_f[0]));
+    const M uy = fmad(jy, inv, M(0.5) * param<M>(p.g[1], p.g_f[1]));
+    const M uz = fmad(jz, inv, M(0.5) * param<M>(p.g[2], p.g_f[2]));
+    const M om = param<M>(p.omega, p.omega_f);
+    const M omm = param<M>(p.omega_m, p.omega_m_f);
     const M uu15 = M(1.5) * fmad(ux, ux, fmad(uy, uy, uz * uz));
     M Fx = 0, Fy = 0, Fz = 0, uF = 0, pref = 0, pref_m = 0;
     if (FORCE) {
-        Fx = rho * (M)p.g[0];
-        Fy = rho * (M)p.g[1];
-        Fz = rho * (M)p.g[2];
+        Fx = rho * param<M>(p.g[0], p.g_f[0]);
+        Fy = rho * param<M>(p.g[1], p.g_f[1]);
+        Fz = rho * param<M>(p.g[2], p.g_f[2]);
         uF = fmad(ux, Fx, fmad(uy, Fy, uz * Fz));
         pref = fmad(M(-0.5), om, M(1));
         pref_m = fmad(M(-0.5), omm, M(1));
