@@ -78,7 +78,22 @@ typedef struct lb_options {
     int storage;       /* lb_storage; default LB_F32 */
     int kernel;        /* step kernel variant: 0 = library's choice */
     int block;         /* threads per block of the step kernel; 0 = choice */
-    int reserved0;
+    int rounding;      /* how a step rounds the new 16-bit stored values
+                          (LB_F16S, LB_BF16S; must be 0 for other storage):
+                          0 (default) to nearest even; 1 stochastically --
+                          up with probability equal to the dropped fraction,
+                          so each stored value is unbiased and changes far
+                          below the 16-bit resolution (a weak body force)
+                          are kept on average instead of lost.  The random
+                          bits are a hash of (cell, direction, steps taken),
+                          so a run is reproducible, every step variant and
+                          batch slot gives bitwise the same result, and a
+                          checkpoint restores the stream with the step
+                          count.  Supported by step variants 1-3, 13, 15,
+                          16, 17 and the in-place kernels; other variants
+                          run 15 (1 where it does not apply).  Equilibrium
+                          initialisation and population import round to
+                          nearest even. */
     double force[3];   /* body force per unit mass g (Guo forcing, the S_i
                           of Eq. 1); default 0 */
     void *stream;      /* cudaStream_t to issue work on; NULL = default */
@@ -103,7 +118,17 @@ typedef struct lb_options {
                           any other variant one cell per thread.  Values
                           that lb_get_populations reports for solid cells
                           are the rest state f = w. */
-    int reserved[5];
+    int halo_z;        /* 0 (default): an ordinary lattice.  1: one z-slab
+                          of a lattice decomposed along z over several GPUs
+                          (the multi-GPU extension that Sec. 6 names as
+                          future work): planes z = 0 and z = nz - 1 are
+                          ghost planes holding the neighbouring slabs'
+                          boundary planes (their flags are the neighbours'
+                          flags; see lb_halo_pack).  The own planes are
+                          1 .. nz-2; lb_totals sums only them and
+                          lb_moments reports 0 on the ghost planes.  Needs
+                          two population arrays (inplace = 0) and nz >= 3. */
+    int reserved[4];
 } lb_options;
 
 /* Fill *opt with the defaults (FP32, no force, default stream). */
@@ -231,23 +256,29 @@ int lb_autotune(lb_lattice *h, int reps, int *variant, int *block, float *ms_per
  * populations in their own buffers).  Same result as lb_totals.
  *   populations  device, 19 planes of plane_stride >= N elements of the
  *                storage type, each value the deviation f_i - w_i, library
- *                velocity order (the layout lb_create uses);
+ *                velocity order, plane i holding direction i (the
+ *                two-array layout of a lattice with lb_options.inplace = 0).
+ *                The arrays of an in-place lattice keep their values in
+ *                other places and are not accepted: the totals would be
+ *                wrong without any error;
  *   flags        device, N bytes, LB_FLUID/LB_WALL/LB_LID/LB_FARFIELD (the
  *                two low bits are read);
  *   force, u_lid host, 3 doubles each or NULL (= 0);
- *   stream       cudaStream_t or NULL; the call synchronises it;
+ *   stream       cudaStream_t or NULL; the call copies the result to host
+ *                memory and synchronises the stream, so it must never be
+ *                called on a stream that is being captured;
  *   out          host, 5 doubles: mass, momentum x/y/z, count of fluid
  *                cells with non-finite or non-positive density.
  * The reduction's scratch is a static device array of
  * LB_STATIC_MAX_BLOCKS * 6 + 8 doubles (about 58 KB) that every GPU loading
  * the library holds until exit; the kernel strides over the lattice with at
  * most LB_STATIC_MAX_BLOCKS blocks, so any lattice below 2^31 cells fits and
- * larger ones are rejected (LB_EINVAL).  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  The array is
- * shared by all calls and keeps the last call's values: calls that overlap
- * on the GPU race on it and must be serialised by the caller.  Calls no
- * cudaMalloc or cudaFree.  Returns LB_OK, LB_EINVAL, LB_ECUDA, or
+ * larger ones are rejected (LB_EINVAL).  Every call looks up the array's
+ * device address (cudaGetSymbolAddress) in the current device's context,
+ * so a device reset or a context switch between calls is harmless.  The
+ * array is shared by all calls and keeps the last call's values: calls
+ * that overlap on the GPU race on it and must be serialised by the caller.
+ * Calls no cudaMalloc or cudaFree.  Returns LB_OK, LB_EINVAL, LB_ECUDA, or
  * LB_EDIVERGED (after filling out). */
 #define LB_STATIC_MAX_BLOCKS 1216
 int lb_totals_static(const void *populations, int64_t plane_stride, const uint8_t *flags,
@@ -348,6 +379,31 @@ const char *lb_batch_last_error(void);
  * as designed (the expected result), LB_EINVAL for a bad deadline,
  * LB_ENOMEM / LB_ECUDA on CUDA failures.  The device context stays usable. */
 int lb_selftest_wait(double seconds, void *stream);
+
+/* Halo exchange of a z-slab lattice (lb_options.halo_z = 1).  A step pulls
+ * the five populations with c_z = +1 into the lowest own plane (z = 1)
+ * from the ghost plane z = 0, and the five with c_z = -1 into the highest
+ * own plane (z = nz - 2) from the ghost plane z = nz - 1; nothing else of
+ * a ghost plane is read.  So between steps each slab sends the rank below
+ * its lowest own plane's c_z = -1 populations and the rank above its
+ * highest own plane's c_z = +1 populations (periodic in z: the last rank's
+ * "above" is rank 0), and writes what it receives into its ghost planes.
+ * A message is those five populations' planes back to back, in the
+ * library's velocity order: 5 * nx * ny values of the storage type,
+ * lb_halo_bytes() bytes (0 for a lattice without ghost planes).
+ *   lb_halo_pack    send_lo <- z = 1, c_z = -1 (for the rank below);
+ *                   send_hi <- z = nz - 2, c_z = +1 (for the rank above);
+ *   lb_halo_unpack  ghost z = 0, c_z = +1 <- recv_lo (the rank below's
+ *                   send_hi); ghost z = nz - 1, c_z = -1 <- recv_hi (the
+ *                   rank above's send_lo).
+ * Buffers are device pointers owned by the caller (suitably aligned for the
+ * storage type).  Both calls are asynchronous on the lattice's stream and
+ * act on the current state (after the last lb_step).  Done after every
+ * step, the slabs together take bitwise the steps of the whole lattice.
+ * Errors: LB_EINVAL (NULL, or no ghost planes), LB_ECUDA. */
+size_t lb_halo_bytes(lb_lattice *h);
+int lb_halo_pack(lb_lattice *h, void *send_lo, void *send_hi);
+int lb_halo_unpack(lb_lattice *h, const void *recv_lo, const void *recv_hi);
 
 /* Wait for all work issued on the lattice's stream.  Returns LB_ETIMEOUT
  * (and clears the condition) if a kernel's bounded wait on an asynchronous

@@ -23,12 +23,13 @@ class LbOptions(ctypes.Structure):
         ("storage", ctypes.c_int),
         ("kernel", ctypes.c_int),
         ("block", ctypes.c_int),
-        ("reserved0", ctypes.c_int),
+        ("rounding", ctypes.c_int),
         ("force", ctypes.c_double * 3),
         ("stream", ctypes.c_void_p),
         ("trt_magic", ctypes.c_double),
         ("inplace", ctypes.c_int),
-        ("reserved", ctypes.c_int * 5),
+        ("halo_z", ctypes.c_int),
+        ("reserved", ctypes.c_int * 4),
     ]
 
 
@@ -87,6 +88,9 @@ SIGNATURES = {
     "lb_batch_sync": (_I, [_P]),
     "lb_batch_destroy": (_I, [_P]),
     "lb_batch_last_error": (ctypes.c_char_p, []),
+    "lb_halo_bytes": (_S, [_P]),
+    "lb_halo_pack": (_I, [_P, _P, _P]),
+    "lb_halo_unpack": (_I, [_P, _P, _P]),
     "lb_selftest_wait": (_I, [_D, _P]),
     "lb_sync": (_I, [_P]),
     "lb_query": (_I, [_P, _P, _P, _P]),

@@ -72,6 +72,12 @@ class Batch:
             _bcheck(st, "lb_batch_destroy")
         self._buf = None
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
     def __del__(self):
         try:
             self.close()
@@ -80,12 +86,12 @@ class Batch:
 
     # ------------------------------------------------------------------
     def add(self, nx, ny, nz, tau, steps, u_lid=(0.0, 0.0, 0.0), flags=None, storage="f32",
-            force=(0.0, 0.0, 0.0), trt_magic=0.0, inplace=False) -> int:
+            force=(0.0, 0.0, 0.0), trt_magic=0.0, inplace=False, rounding="nearest") -> int:
         """Admit a lattice; returns its slot.  Raises LbError with status
         LB_ENOMEM (pool full) or LB_EBUSY (no free slot) when it does not fit.
         trt_magic > 0 selects the two-relaxation-time collision; inplace keeps
         one population array (half the population memory)."""
-        opts = make_options(storage, force, trt_magic=trt_magic, inplace=inplace)
+        opts = make_options(storage, force, trt_magic=trt_magic, inplace=inplace, rounding=rounding)
         ulid = (ctypes.c_double * 3)(*[float(v) for v in u_lid])
         fl = None
         if flags is not None:

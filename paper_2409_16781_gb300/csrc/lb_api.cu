@@ -37,6 +37,8 @@ struct lb_lattice {
     int kernel, block;
     int64_t steps;
     bool walls;  // some flag is not LB_FLUID: cells next to a wall exist
+    int halo_z;  // z-slab: planes 0 and nz-1 are ghost planes (lb_options.halo_z)
+    int rounding;  // 16-bit storage: 0 nearest even, 1 stochastic (lb_options.rounding)
 };
 
 namespace {
@@ -118,6 +120,10 @@ LatticeParams params_of(const lb_lattice* h) {
     }
     set_farfield(p);
     p.err = h->err;
+    p.zlo = h->halo_z ? 1 : 0;
+    p.zhi = h->halo_z ? h->nz - 1 : h->nz;
+    p.sr = h->rounding;
+    p.sr_seed = sr_seed(h->steps);
     return p;
 }
 
@@ -152,6 +158,13 @@ int create_common(lb_lattice** out, int nx, int ny, int nz, double tau, const do
     if (!(o.trt_magic >= 0.0) || !std::isfinite(o.trt_magic))
         return fail(LB_EINVAL, "lb_create: trt_magic must be >= 0 (got %g)", o.trt_magic);
     if (o.inplace != 0 && o.inplace != 1) return fail(LB_EINVAL, "lb_create: inplace must be 0 or 1 (got %d)", o.inplace);
+    if (o.halo_z != 0 && o.halo_z != 1) return fail(LB_EINVAL, "lb_create: halo_z must be 0 or 1 (got %d)", o.halo_z);
+    if (o.rounding != 0 && o.rounding != 1) return fail(LB_EINVAL, "lb_create: rounding must be 0 or 1 (got %d)", o.rounding);
+    if (o.rounding && storage_bytes(o.storage) != 2)
+        return fail(LB_EINVAL, "lb_create: stochastic rounding needs 16-bit storage (got storage %d)", o.storage);
+    if (o.halo_z && (o.inplace || nz < 3))
+        return fail(LB_EINVAL, "lb_create: a z-slab (halo_z) needs two population arrays and nz >= 3 (got inplace %d, "
+                    "nz %d)", o.inplace, nz);
     for (int a = 0; a < 3; ++a) {
         if (!std::isfinite(o.force[a])) return fail(LB_EINVAL, "lb_create: non-finite force");
         if (u_lid && !std::isfinite(u_lid[a])) return fail(LB_EINVAL, "lb_create: non-finite u_lid");
@@ -201,6 +214,8 @@ int create_common(lb_lattice** out, int nx, int ny, int nz, double tau, const do
     }
     char* b = (char*)h->base;
     h->inplace = o.inplace;
+    h->halo_z = o.halo_z;
+    h->rounding = o.rounding;
     h->walls = walls;
     h->form = o.inplace ? FORM_SWAPPED : FORM_AB;
     h->pop[0] = b;
@@ -314,8 +329,9 @@ int lb_init_fields(lb_lattice* h, const double* rho, const double* u) {
 int lb_step(lb_lattice* h, int n) {
     if (!h) return fail(LB_EINVAL, "lb_step: NULL handle");
     if (n < 0) return fail(LB_EINVAL, "lb_step: n < 0");
-    const LatticeParams p = params_of(h);
+    LatticeParams p = params_of(h);
     for (int t = 0; t < n; ++t) {
+        p.sr_seed = sr_seed(h->steps);
         if (h->inplace) {
             cudaError_t e = launch_step_inplace(h->storage, h->kernel, h->pop[0], h->code, p, h->form, h->block,
                                                 h->stream);
@@ -577,12 +593,15 @@ int lb_autotune(lb_lattice* h, int reps, int* variant, int* block, float* ms_per
         if (nc < 32) cands[nc++] = {v, b};
     };
     const bool sixteen = h->sbytes == 2;
+    // stochastic rounding: only the variants that have that form (the others
+    // would run variant 15)
+    const bool all = !h->rounding;
     if (h->inplace) return autotune_inplace(h, reps, variant, block, ms_per_step);
     for (int b : {32, 64, 128, 256}) add(1, b);
-    if (h->nx % 2 == 0) {
+    if (h->nx % 2 == 0 && all) {
         for (int b : {64, 128}) add(sixteen ? 6 : 4, b);
     }
-    if (sixteen && h->nx % 4 == 0) {
+    if (sixteen && h->nx % 4 == 0 && all) {
         for (int b : {32, 64, 128}) add(8, b);
         for (int b : {32, 64, 128}) add(14, b);
     }
@@ -594,7 +613,7 @@ int lb_autotune(lb_lattice* h, int reps, int* variant, int* block, float* ms_per
     if (h->walls) {
         for (int b : {64, 128}) add(16, b);
     }
-    if (sixteen && h->nx % 16 == 0) {
+    if (sixteen && h->nx % 16 == 0 && all) {
         add(10, 0);
         add(11, 0);
         add(12, 0);
@@ -634,6 +653,26 @@ int lb_autotune(lb_lattice* h, int reps, int* variant, int* block, float* ms_per
     if (block) *block = h->block;
     if (ms_per_step) *ms_per_step = best_ms / reps;
     return LB_OK;
+}
+
+size_t lb_halo_bytes(lb_lattice* h) {
+    if (!h || !h->halo_z) return 0;
+    return (size_t)5 * h->nx * h->ny * h->sbytes;
+}
+
+int lb_halo_pack(lb_lattice* h, void* send_lo, void* send_hi) {
+    if (!h || !send_lo || !send_hi) return fail(LB_EINVAL, "lb_halo_pack: NULL argument");
+    if (!h->halo_z) return fail(LB_EINVAL, "lb_halo_pack: the lattice has no ghost planes (lb_options.halo_z)");
+    cudaError_t e = launch_halo(h->sbytes, h->pop[h->cur], h->ps, h->nx, h->ny, h->nz, send_lo, send_hi, 1, h->stream);
+    return e == cudaSuccess ? LB_OK : cuda_fail(e, "lb_halo_pack");
+}
+
+int lb_halo_unpack(lb_lattice* h, const void* recv_lo, const void* recv_hi) {
+    if (!h || !recv_lo || !recv_hi) return fail(LB_EINVAL, "lb_halo_unpack: NULL argument");
+    if (!h->halo_z) return fail(LB_EINVAL, "lb_halo_unpack: the lattice has no ghost planes (lb_options.halo_z)");
+    cudaError_t e = launch_halo(h->sbytes, h->pop[h->cur], h->ps, h->nx, h->ny, h->nz, const_cast<void*>(recv_lo),
+                                const_cast<void*>(recv_hi), 0, h->stream);
+    return e == cudaSuccess ? LB_OK : cuda_fail(e, "lb_halo_unpack");
 }
 
 int lb_sync(lb_lattice* h) {

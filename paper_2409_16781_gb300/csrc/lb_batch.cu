@@ -67,14 +67,17 @@ struct SlotDev {
     int inplace;     // parity 0: swapped layout, 1: streamed layout
 };
 
-template <class S, bool FORCE, bool INPLACE>
-__device__ __forceinline__ void update_cell(const SlotDev& sd, int parity, int cell, int x, int y, int z, uint8_t cc) {
+// SR: stochastic rounding of a 16-bit slot (lb_options.rounding), seeded by
+// the slot's step count exactly as a lattice stepped alone is.
+template <class S, bool FORCE, bool INPLACE, bool SR>
+__device__ __forceinline__ void update_cell(const SlotDev& sd, int parity, int cell, int x, int y, int z, uint8_t cc,
+                                            uint32_t seed) {
     using M = typename Storage<S>::math;
     if constexpr (INPLACE) {  // pop[0] and pop[1] are the one array
         const S* Ar = static_cast<const S*>(sd.pop[0]);
         S* Aw = static_cast<S*>(sd.pop[1]);
-        if (parity == 0) inplace_update<S, FORCE, FORM_SWAPPED>(Ar, Aw, sd.code, sd.p, x, y, z, cell, cc);
-        else inplace_update<S, FORCE, FORM_STREAMED>(Ar, Aw, sd.code, sd.p, x, y, z, cell, cc);
+        if (parity == 0) inplace_update<S, FORCE, FORM_SWAPPED, SR>(Ar, Aw, sd.code, sd.p, x, y, z, cell, cc, seed);
+        else inplace_update<S, FORCE, FORM_STREAMED, SR>(Ar, Aw, sd.code, sd.p, x, y, z, cell, cc, seed);
         return;
     }
     const S* A = static_cast<const S*>(sd.pop[parity]);
@@ -85,8 +88,19 @@ __device__ __forceinline__ void update_cell(const SlotDev& sd, int parity, int c
     // still faster on the seeded serving mix)
     pull_cell<S, 0, FORM_AB, true>(A, sd.code, sd.p, x, y, z, cell, cc, d);
     relax_dev<M, FORCE>(d, sd.p);
+    const Rounder<S, SR> R(seed);
+    const uint32_t key = R.key(cell);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) B[(int64_t)i * sd.p.ps + cell] = Storage<S>::store(d[i]);
+    for (int i = 0; i < Q; ++i) B[(int64_t)i * sd.p.ps + cell] = R.one(d[i], key, cell, i);
+}
+
+template <class S, bool INPLACE, bool SR>
+__device__ __forceinline__ void update_cell_f(const SlotDev& sd, int parity, int cell, int x, int y, int z,
+                                              uint8_t cc, uint32_t seed) {
+    if (sd.force)
+        update_cell<S, true, INPLACE, SR>(sd, parity, cell, x, y, z, cc, seed);
+    else
+        update_cell<S, false, INPLACE, SR>(sd, parity, cell, x, y, z, cc, seed);
 }
 
 // One batched step for every active slot of storage type S and one
@@ -98,6 +112,7 @@ template <class S, bool INPLACE>
 __global__ void __launch_bounds__(BATCH_THREADS) batch_step_kernel(const SlotDev* __restrict__ slots,
                                                                    const int* __restrict__ parity,
                                                                    const int64_t* __restrict__ remaining,
+                                                                   const int64_t* __restrict__ done,
                                                                    const int* __restrict__ act,
                                                                    const int* __restrict__ off,
                                                                    const int* __restrict__ nact) {
@@ -137,10 +152,13 @@ __global__ void __launch_bounds__(BATCH_THREADS) batch_step_kernel(const SlotDev
         const uint8_t cc = sd.code[cell];
         if (cc & CODE_TYPE) continue;
         const int par = parity[slot];
-        if (sd.force)
-            update_cell<S, true, INPLACE>(sd, par, cell, x, y, z, cc);
-        else
-            update_cell<S, false, INPLACE>(sd, par, cell, x, y, z, cc);
+        if constexpr (sizeof(S) == 2) {
+            if (sd.p.sr) {
+                update_cell_f<S, INPLACE, true>(sd, par, cell, x, y, z, cc, sr_seed(done[slot]));
+                continue;
+            }
+        }
+        update_cell_f<S, INPLACE, false>(sd, par, cell, x, y, z, cc, 0u);
     }
 }
 
@@ -410,6 +428,7 @@ int rebuild_lists(lb_batch* b) {
 template <class S, bool INPLACE>
 static void launch_typed(lb_batch* b, int t, cudaStream_t st) {
     batch_step_kernel<S, INPLACE><<<b->grid[t], BATCH_THREADS, 0, st>>>(b->d_slots, b->d_parity, b->d_remaining,
+                                                                         b->d_done,
                                                                          b->d_act[t], b->d_off[t], b->d_nact + t);
 }
 
@@ -675,6 +694,10 @@ int lb_batch_add(lb_batch* b, int nx, int ny, int nz, double tau, const double* 
     if (!(o.trt_magic >= 0.0) || !std::isfinite(o.trt_magic))
         return bfail(LB_EINVAL, "lb_batch_add: trt_magic must be >= 0");
     if (o.inplace != 0 && o.inplace != 1) return bfail(LB_EINVAL, "lb_batch_add: inplace must be 0 or 1");
+    if (o.rounding != 0 && o.rounding != 1) return bfail(LB_EINVAL, "lb_batch_add: rounding must be 0 or 1");
+    if (o.rounding && storage_bytes(o.storage) != 2)
+        return bfail(LB_EINVAL, "lb_batch_add: stochastic rounding needs 16-bit storage");
+    if (o.halo_z) return bfail(LB_EINVAL, "lb_batch_add: batch slots have no ghost planes (halo_z)");
     if (steps < 0) return bfail(LB_EINVAL, "lb_batch_add: steps < 0");
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(o.force[a]) || (u_lid && !std::isfinite(u_lid[a])))
@@ -708,6 +731,10 @@ int lb_batch_add(lb_batch* b, int nx, int ny, int nz, double tau, const double* 
     d.p.nz = nz;
     d.p.N = N;
     d.p.ps = ps;
+    d.p.zlo = 0;
+    d.p.zhi = nz;
+    d.p.sr = o.rounding;
+    d.p.sr_seed = 0;  // per step from the slot's step count
     d.p.omega = 1.0 / tau;
     d.p.omega_m = trt_omega_minus(tau, o.trt_magic);
     for (int a = 0; a < 3; ++a) {

@@ -99,6 +99,61 @@ template <> struct Storage<f32d> {
     __device__ __forceinline__ static f32d store(double v) { return f32d{narrow_f64(v)}; }
 };
 
+// Stochastic rounding (SR) of 16-bit stored deviations (lb_options.rounding
+// = 1).  Round-to-nearest drops every change smaller than half a unit in the
+// last place of the stored value, so a small body force, whose increment
+// per step is below that, stalls the flow; SR rounds up with probability
+// equal to the dropped fraction, which keeps every value's expectation and
+// turns the rounding error into noise.  The random bits come from a
+// counter-based hash of (cell pair, direction, step), the same whichever
+// kernel shape stores the value, so every step variant gives the same
+// bits:
+//   key  = fmix32((cell >> 1) ^ seed(step))   (cells 2k and 2k+1 share it)
+//   bits = lo32(key * C_i) ^ hi32(key * C_i)  (per direction i)
+// fmix32 is the 32-bit finalizer of Appleby's MurmurHash3; C_i are odd
+// constants from SplitMix64 (Steele, Lea & Flood 2014) of i + 1.  The
+// hardware conversion (cvt.rs.f16x2 / .bf16x2, sm_100-class GPUs) adds the
+// bits below the kept mantissa and truncates, taking the low half's bits
+// from bits[15:0] and the high half's from bits[31:16] (FP16 the low 13 of
+// each), so cell 2k is always converted in the low half and cell 2k+1 in
+// the high half.
+__host__ __device__ constexpr uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+__host__ __device__ constexpr uint32_t sr_const(int i) {
+    uint64_t z = (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (uint32_t)z | 1u;
+}
+// Seed of the step that takes a lattice from `step` to step + 1 steps.
+__host__ __device__ constexpr uint32_t sr_seed(int64_t step) {
+    return fmix32((uint32_t)step * 0x9E3779B9u ^ fmix32((uint32_t)((uint64_t)step >> 32) + 0x632BE5ABu));
+}
+__device__ __forceinline__ uint32_t sr_key(int cell, uint32_t seed) { return fmix32(((uint32_t)cell >> 1) ^ seed); }
+__device__ __forceinline__ uint32_t sr_bits(uint32_t key, int i) {
+    const uint64_t m = (uint64_t)key * sr_const(i);
+    return (uint32_t)m ^ (uint32_t)(m >> 32);
+}
+// The two values packed as (lo | hi << 16), stochastically rounded.
+template <class S> __device__ __forceinline__ uint32_t cvt_rs2(float lo, float hi, uint32_t bits);
+template <> __device__ __forceinline__ uint32_t cvt_rs2<__half>(float lo, float hi, uint32_t bits) {
+    uint32_t r;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(r) : "f"(hi), "f"(lo), "r"(bits));
+    return r;
+}
+template <> __device__ __forceinline__ uint32_t cvt_rs2<__nv_bfloat16>(float lo, float hi, uint32_t bits) {
+    uint32_t r;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(r) : "f"(hi), "f"(lo), "r"(bits));
+    return r;
+}
+
 // Parameters of one lattice as seen by the kernels.
 struct LatticeParams {
     int nx, ny, nz;
@@ -110,6 +165,15 @@ struct LatticeParams {
     double ulid[3];   // lid velocity (and free-stream velocity of far-field cells)
     double ff[19];    // far-field deviations f^eq_i(1, ulid) - w_i (set_farfield)
     int* err;         // device error word (bounded waits that gave up), or nullptr
+    // z-planes [zlo, zhi) hold the lattice's own cells; the totals and the
+    // moments cover only them.  A z-slab of a decomposed lattice keeps a
+    // ghost plane below and above (zlo = 1, zhi = nz - 1) whose inward
+    // populations are the neighbouring slabs' values; otherwise 0 and nz.
+    int zlo, zhi;
+    // rounding of 16-bit stored values: 0 nearest even, 1 stochastic with
+    // the step's seed (sr_seed of the steps taken before this one)
+    int sr;
+    uint32_t sr_seed;
     // omega, omega_m and g rounded to FP32 on the host (set_farfield): the
     // FP32-arithmetic kernels read these instead of converting the FP64
     // fields in every thread (a GB300 runs that conversion on its narrow

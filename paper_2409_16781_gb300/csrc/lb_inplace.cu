@@ -28,7 +28,7 @@ namespace lbgb {
 // follow it) only so that the compiler does not keep the 19 load addresses
 // live through the collision to reuse them for the stores: it recomputes the
 // store addresses instead, which leaves more registers for more warps.
-template <class S, bool FORCE, int FORM>
+template <class S, bool FORCE, int FORM, bool SR>
 __global__ void __launch_bounds__(512) step_kernel_inplace(const S* Ar, S* Aw, const uint8_t* __restrict__ code,
                                                            LatticeParams p, int xblocks) {
     const int xb = blockIdx.x % xblocks;
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(512) step_kernel_inplace(const S* Ar, S* Aw, c
     const int cell = x + p.nx * row;
     const uint8_t cc = code[cell];
     if (cc & CODE_TYPE) return;  // solid cells hold no values of their own
-    inplace_update<S, FORCE, FORM>(Ar, Aw, code, p, x, y, z, cell, cc);
+    inplace_update<S, FORCE, FORM, SR>(Ar, Aw, code, p, x, y, z, cell, cc, p.sr_seed);
 }
 
 // ---------------------------------------------------------------------------
@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(512) step_kernel_inplace(const S* Ar, S* Aw, c
 //     x-shift would break the alignment.
 // Solid cells of a pair store nothing (as in the one-cell kernel).
 // ---------------------------------------------------------------------------
-template <class S, bool FORCE, int FORM>
+template <class S, bool FORCE, int FORM, bool SR>
 __global__ void __launch_bounds__(128, 8) step_kernel_inplace_pairs(const S* Ar, S* Aw,
                                                                     const uint8_t* __restrict__ code,
                                                                     LatticeParams p, int xblocks) {
@@ -110,16 +110,28 @@ __global__ void __launch_bounds__(128, 8) step_kernel_inplace_pairs(const S* Ar,
     if (!f0 && !f1) return;  // solid cells hold no values of their own
     bounce_fix_x2<S, 0, FORM>(Ar, code, p, x0, y, z, cell0, c0, c1, d);
     relax_dev<f32x2, FORCE>(d, p);
+    // each value is rounded by the cell that computed it (cell0 or
+    // cell0 + 1), wherever it is stored
+    const Rounder<S, SR> R(p.sr_seed);
+    const uint32_t key = R.key(cell0);
+    auto pair_word = [&](int i) {
+        if constexpr (SR) return R.two(d[i].v.x, d[i].v.y, key, i);
+        else return pack2<S>(d[i].v.x, d[i].v.y);
+    };
+    auto pair_store = [&](S* q, int i) {
+        if constexpr (SR) st_pop<0>(reinterpret_cast<uint32_t*>(q), pair_word(i));
+        else st_pop<0>(reinterpret_cast<V*>(q), pair_word(i));
+    };
     if constexpr (FORM == FORM_STREAMED) {
         // -> FORM_SWAPPED: P_i(x) into plane opp(i) at x
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             S* q = Aw + (int64_t)D3Q19::opp(i) * p.ps + cell0;
             if (f0 && f1) {
-                st_pop<0>(reinterpret_cast<V*>(q), pack2<S>(d[i].v.x, d[i].v.y));
+                pair_store(q, i);
             } else {
-                if (f0) st_pop<0>(q, Storage<S>::store(d[i].v.x));
-                if (f1) st_pop<0>(q + 1, Storage<S>::store(d[i].v.y));
+                if (f0) st_pop<0>(q, R.one(d[i].v.x, key, cell0, i));
+                if (f1) st_pop<0>(q + 1, R.one(d[i].v.y, key, cell0 + 1, i));
             }
         }
     } else {
@@ -131,23 +143,23 @@ __global__ void __launch_bounds__(128, 8) step_kernel_inplace_pairs(const S* Ar,
             S* rowt = Aw + (int64_t)i * p.ps + yt[D3Q19::cy(i) + 1] + zt[D3Q19::cz(i) + 1];
             if (D3Q19::cx(i) == 0) {
                 if (f0 && f1) {
-                    st_pop<0>(reinterpret_cast<V*>(rowt + x0), pack2<S>(d[i].v.x, d[i].v.y));
+                    pair_store(rowt + x0, i);
                 } else {
-                    if (f0) st_pop<0>(rowt + x0, Storage<S>::store(d[i].v.x));
-                    if (f1) st_pop<0>(rowt + x0 + 1, Storage<S>::store(d[i].v.y));
+                    if (f0) st_pop<0>(rowt + x0, R.one(d[i].v.x, key, cell0, i));
+                    if (f1) st_pop<0>(rowt + x0 + 1, R.one(d[i].v.y, key, cell0 + 1, i));
                 }
             } else if (D3Q19::cx(i) == 1) {  // targets x0 + 1, x0 + 2
-                if (f0) st_pop<0>(rowt + x0 + 1, Storage<S>::store(d[i].v.x));
-                if (f1) st_pop<0>(rowt + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2), Storage<S>::store(d[i].v.y));
+                if (f0) st_pop<0>(rowt + x0 + 1, R.one(d[i].v.x, key, cell0, i));
+                if (f1) st_pop<0>(rowt + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2), R.one(d[i].v.y, key, cell0 + 1, i));
             } else {  // targets x0 - 1, x0
-                if (f0) st_pop<0>(rowt + (x0 == 0 ? nx - 1 : x0 - 1), Storage<S>::store(d[i].v.x));
-                if (f1) st_pop<0>(rowt + x0, Storage<S>::store(d[i].v.y));
+                if (f0) st_pop<0>(rowt + (x0 == 0 ? nx - 1 : x0 - 1), R.one(d[i].v.x, key, cell0, i));
+                if (f1) st_pop<0>(rowt + x0, R.one(d[i].v.y, key, cell0 + 1, i));
             }
         }
     }
 }
 
-template <class S, int FORM>
+template <class S, int FORM, bool SR>
 static cudaError_t step_inplace_pairs_form(void* A, const uint8_t* code, const LatticeParams& p, int block,
                                            cudaStream_t st) {
     int bx = block > 0 ? (block / 32) * 32 : 64;  // whole warps (the shuffles need all 32 lanes)
@@ -160,15 +172,15 @@ static cudaError_t step_inplace_pairs_form(void* A, const uint8_t* code, const L
     const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if (force)
-        step_kernel_inplace_pairs<S, true, FORM>
+        step_kernel_inplace_pairs<S, true, FORM, SR>
             <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);
     else
-        step_kernel_inplace_pairs<S, false, FORM>
+        step_kernel_inplace_pairs<S, false, FORM, SR>
             <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);
     return cudaGetLastError();
 }
 
-template <class S, int FORM>
+template <class S, int FORM, bool SR>
 static cudaError_t step_inplace_form(void* A, const uint8_t* code, const LatticeParams& p, int block,
                                      cudaStream_t st) {
     int bx = block > 0 ? (block / 32) * 32 : 128;
@@ -180,27 +192,37 @@ static cudaError_t step_inplace_form(void* A, const uint8_t* code, const Lattice
     const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if (force)
-        step_kernel_inplace<S, true, FORM><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);
+        step_kernel_inplace<S, true, FORM, SR><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);
     else
-        step_kernel_inplace<S, false, FORM><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);
+        step_kernel_inplace<S, false, FORM, SR><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);
     return cudaGetLastError();
 }
 
 // Variants of an in-place lattice: 2 = two cells per thread in packed FP32
 // (FP32 or 16-bit storage, nx even); anything else one cell per thread.
-template <class S>
-static cudaError_t step_inplace_t(int variant, void* A, const uint8_t* code, const LatticeParams& p, int form,
+// SR: the stochastically rounding form (16-bit storage, p.sr).
+template <class S, bool SR>
+static cudaError_t step_inplace_r(int variant, void* A, const uint8_t* code, const LatticeParams& p, int form,
                                   int block, cudaStream_t st) {
     if constexpr (std::is_same<S, float>::value || sizeof(S) == 2) {
         if (variant == 2 && p.nx % 2 == 0) {
-            if (form == FORM_SWAPPED) return step_inplace_pairs_form<S, FORM_SWAPPED>(A, code, p, block, st);
-            if (form == FORM_STREAMED) return step_inplace_pairs_form<S, FORM_STREAMED>(A, code, p, block, st);
+            if (form == FORM_SWAPPED) return step_inplace_pairs_form<S, FORM_SWAPPED, SR>(A, code, p, block, st);
+            if (form == FORM_STREAMED) return step_inplace_pairs_form<S, FORM_STREAMED, SR>(A, code, p, block, st);
             return cudaErrorInvalidValue;
         }
     }
-    if (form == FORM_SWAPPED) return step_inplace_form<S, FORM_SWAPPED>(A, code, p, block, st);
-    if (form == FORM_STREAMED) return step_inplace_form<S, FORM_STREAMED>(A, code, p, block, st);
+    if (form == FORM_SWAPPED) return step_inplace_form<S, FORM_SWAPPED, SR>(A, code, p, block, st);
+    if (form == FORM_STREAMED) return step_inplace_form<S, FORM_STREAMED, SR>(A, code, p, block, st);
     return cudaErrorInvalidValue;
+}
+
+template <class S>
+static cudaError_t step_inplace_t(int variant, void* A, const uint8_t* code, const LatticeParams& p, int form,
+                                  int block, cudaStream_t st) {
+    if constexpr (sizeof(S) == 2) {
+        if (p.sr) return step_inplace_r<S, true>(variant, A, code, p, form, block, st);
+    }
+    return step_inplace_r<S, false>(variant, A, code, p, form, block, st);
 }
 
 #ifdef LBGB_CHECKED

@@ -21,6 +21,11 @@ cudaError_t launch_moments(int storage, const void* A, const uint8_t* code, cons
 int totals_blocks(int64_t N);
 cudaError_t launch_totals(int storage, const void* A, const uint8_t* code, const LatticeParams& p,
                           double* partials, double* out5, cudaStream_t st, int form = 0);
+// The same totals from a plain flag field (no cell codes) over populations
+// in the two-array layout, with at most max_blocks partial sums (6 doubles
+// each) in `partials`: every fluid cell checks its pull sources.
+cudaError_t launch_totals_flags(int storage, const void* A, const uint8_t* flags, const LatticeParams& p,
+                                double* partials, int max_blocks, double* out5, cudaStream_t st);
 cudaError_t launch_get_pops(int storage, const void* A, const uint8_t* code, const LatticeParams& p, int form,
                             int64_t c0, int64_t count, double* buf, cudaStream_t st);
 cudaError_t launch_set_pops(int storage, void* A, void* B, int64_t ps, int64_t c0, int64_t count,
@@ -31,6 +36,15 @@ cudaError_t launch_gather_pops(int storage, const void* A, const uint8_t* code, 
 // FORM_STREAMED) to the other layout, one array.
 cudaError_t launch_step_inplace(int storage, int variant, void* A, const uint8_t* code, const LatticeParams& p,
                                 int form, int block, cudaStream_t st);
+
+// Halo planes of a z-slab (lb_halo.cu): pack != 0 copies the lowest own
+// plane's c_z = -1 populations (z = 1) to lo and the highest own plane's
+// c_z = +1 populations (z = nz - 2) to hi; pack == 0 copies lo into the
+// c_z = +1 populations of the ghost plane z = 0 and hi into the c_z = -1
+// populations of the ghost plane z = nz - 1.  lo and hi hold 5 * nx * ny
+// values of sbytes bytes each.
+cudaError_t launch_halo(int sbytes, void* A, int64_t ps, int nx, int ny, int nz, void* lo, void* hi, int pack,
+                        cudaStream_t st);
 
 // Instantiate CALL with S = the storage type of `storage` and return it.
 #ifdef LBGB_CHECKED

@@ -86,8 +86,9 @@ __global__ void moments_kernel(const S* __restrict__ A, const uint8_t* __restric
         const int cell = (int)(c0 + k);
         const uint8_t cc = code[cell];
         double r = 0, vx = 0, vy = 0, vz = 0;
-        if (!(cc & CODE_TYPE)) {
-            const int x = cell % p.nx, y = (cell / p.nx) % p.ny, z = cell / (p.nx * p.ny);
+        const int z = cell / (p.nx * p.ny);
+        if (!(cc & CODE_TYPE) && z >= p.zlo && z < p.zhi) {
+            const int x = cell % p.nx, y = (cell / p.nx) % p.ny;
             M d[Q];
             pull_cell<S, 0, FORM>(A, code, p, x, y, z, cell, cc, d);
             M drho, mr, ux, uy, uz;
@@ -115,28 +116,31 @@ __global__ void moments_kernel(const S* __restrict__ A, const uint8_t* __restric
 // kernel adds the partials in a fixed order, so the result is reproducible.
 //   mass = n_fluid + sum drho,  momentum = sum j + (g/2) mass
 // (rho u = j + rho g/2 with the half-force shift).
+// FLAGS: `code` is a plain flag field (values 0-3, no "next to a wall" bit,
+// as lb_totals_static receives it), so every fluid cell checks its 18 pull
+// sources for bounce-back.
 // ---------------------------------------------------------------------------
 constexpr int TOT_THREADS = 256;
 constexpr int TOT_FOLD = 8;
 constexpr int TOT_PARTS = 6;
 
-template <class S, int FORM>
+template <class S, int FORM, bool FLAGS = false>
 __global__ void __launch_bounds__(TOT_THREADS) totals_kernel(const S* __restrict__ A,
                                                              const uint8_t* __restrict__ code,
                                                              LatticeParams p, double* __restrict__ partials) {
     using M = typename Storage<S>::math;
     double acc[TOT_PARTS] = {0, 0, 0, 0, 0, 0};
     const int xblocks = (p.nx + TOT_THREADS - 1) / TOT_THREADS;
-    const int64_t items = (int64_t)xblocks * p.ny * p.nz;
+    const int64_t items = (int64_t)xblocks * p.ny * (p.zhi - p.zlo);
     M sd = 0, sx = 0, sy = 0, sz = 0;
     int nf = 0, nbad = 0, pending = 0;
     for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
         const int xb = (int)(it % xblocks);
-        const int row = (int)(it / xblocks);
+        const int row = p.zlo * p.ny + (int)(it / xblocks);
         const int x = xb * TOT_THREADS + threadIdx.x;
         if (x < p.nx) {
             const int cell = x + p.nx * row;
-            const uint8_t cc = code[cell];
+            const uint8_t cc = FLAGS ? (uint8_t)(code[cell] | CODE_NEAR_WALL) : code[cell];
             if (!(cc & CODE_TYPE)) {
                 M d[Q];
                 pull_cell<S, 0, FORM>(A, code, p, x, row % p.ny, row / p.ny, cell, cc, d);
@@ -337,6 +341,22 @@ static cudaError_t totals_t(const void* A, const uint8_t* code, const LatticePar
 cudaError_t launch_totals(int storage, const void* A, const uint8_t* code, const LatticeParams& p,
                           double* partials, double* out5, cudaStream_t st, int form) {
     LBGB_DISPATCH(storage, totals_t<S>(A, code, p, partials, out5, form, st));
+}
+
+template <class S>
+static cudaError_t totals_flags_t(const void* A, const uint8_t* flags, const LatticeParams& p, double* partials,
+                                  int max_blocks, double* out5, cudaStream_t st) {
+    int nb = totals_blocks(p.N);
+    if (nb > max_blocks) nb = max_blocks;
+    totals_kernel<S, FORM_AB, true><<<nb, TOT_THREADS, 0, st>>>((const S*)A, flags, p, partials);
+    totals_finalize_kernel<<<1, TOT_THREADS, 0, st>>>(partials, nb, p, out5);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_totals_flags(int storage, const void* A, const uint8_t* flags, const LatticeParams& p,
+                                double* partials, int max_blocks, double* out5, cudaStream_t st) {
+    if (max_blocks < 1) return cudaErrorInvalidValue;
+    LBGB_DISPATCH(storage, totals_flags_t<S>(A, flags, p, partials, max_blocks, out5, st));
 }
 
 template <class S>

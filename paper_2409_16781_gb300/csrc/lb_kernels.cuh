@@ -505,21 +505,71 @@ __device__ __forceinline__ void relax_dev(M (&d)[Q], const LatticeParams& p) {
     for (int i = 0; i < Q; ++i) d[i] = out[i];
 }
 
+// How a step kernel rounds a new value into the storage type S: to nearest
+// even (SR = false: Storage<S>::store), or stochastically (SR = true, 16-bit
+// storage only: sr_key / sr_bits / cvt_rs2 of lb_common.cuh, with the
+// launch's seed).  `key` is the cell pair's hash (key(cell)); a value is
+// rounded by the cell that computed it, wherever it is stored.
+template <class S> __device__ __forceinline__ S from_bits16(uint32_t w);
+template <> __device__ __forceinline__ __half from_bits16<__half>(uint32_t w) {
+    return __ushort_as_half((unsigned short)w);
+}
+template <> __device__ __forceinline__ __nv_bfloat16 from_bits16<__nv_bfloat16>(uint32_t w) {
+    return __ushort_as_bfloat16((unsigned short)w);
+}
+
+template <class S, bool SR>
+struct Rounder {
+    static_assert(!SR || sizeof(S) == 2, "stochastic rounding is for 16-bit storage");
+    uint32_t seed;
+    __device__ __forceinline__ explicit Rounder(uint32_t step_seed) : seed(step_seed) {}
+    __device__ __forceinline__ uint32_t key(int cell) const {
+        if constexpr (SR) return sr_key(cell, seed);
+        else return 0u;
+    }
+    // value v of direction i of cell `cell`
+    __device__ __forceinline__ S one(typename Storage<S>::math v, uint32_t key, int cell, int i) const {
+        if constexpr (SR) {
+            const uint32_t b = sr_bits(key, i);
+            return from_bits16<S>((cell & 1) ? cvt_rs2<S>(0.f, v, b) >> 16 : cvt_rs2<S>(v, 0.f, b));
+        } else {
+            return Storage<S>::store(v);
+        }
+    }
+    // direction i of the even cell (lo) and the next one (hi), packed into
+    // one 32-bit word (16-bit storage)
+    __device__ __forceinline__ uint32_t two(float lo, float hi, uint32_t key, int i) const {
+        static_assert(sizeof(S) == 2, "packed pairs are 16-bit");
+        if constexpr (SR) {
+            return cvt_rs2<S>(lo, hi, sr_bits(key, i));
+        } else if constexpr (std::is_same<S, __half>::value) {
+            const __half2 h = __floats2half2_rn(lo, hi);
+            return *reinterpret_cast<const uint32_t*>(&h);
+        } else {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+            return *reinterpret_cast<const uint32_t*>(&h);
+        }
+    }
+};
+
 // One in-place ("AA") update of fluid cell (x, y, z) whose state has layout
 // FORM (FORM_SWAPPED or FORM_STREAMED): pull, collide, and store in the other
 // layout -- from FORM_STREAMED into plane opp(i) at the cell, from
 // FORM_SWAPPED into plane i at x + c_i (periodic wrap).  Ar and Aw are the
 // same array (see step_kernel_inplace for why they are two pointers).
-template <class S, bool FORCE, int FORM>
+template <class S, bool FORCE, int FORM, bool SR = false>
 __device__ __forceinline__ void inplace_update(const S* Ar, S* Aw, const uint8_t* __restrict__ code,
-                                               const LatticeParams& p, int x, int y, int z, int cell, uint8_t cc) {
+                                               const LatticeParams& p, int x, int y, int z, int cell, uint8_t cc,
+                                               uint32_t seed = 0) {
     using M = typename Storage<S>::math;
     M d[Q];
     pull_cell<S, 0, FORM>(Ar, code, p, x, y, z, cell, cc, d);
     relax_dev<M, FORCE>(d, p);
+    const Rounder<S, SR> R(seed);
+    const uint32_t key = R.key(cell);
     if constexpr (FORM == FORM_STREAMED) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) st_pop<0>(Aw + (int64_t)D3Q19::opp(i) * p.ps + cell, Storage<S>::store(d[i]));
+        for (int i = 0; i < Q; ++i) st_pop<0>(Aw + (int64_t)D3Q19::opp(i) * p.ps + cell, R.one(d[i], key, cell, i));
     } else {
         const int nx = p.nx, ny = p.ny, nz = p.nz;
         const int nxy = nx * ny;
@@ -529,7 +579,7 @@ __device__ __forceinline__ void inplace_update(const S* Ar, S* Aw, const uint8_t
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const int t = xt[D3Q19::cx(i) + 1] + yt[D3Q19::cy(i) + 1] + zt[D3Q19::cz(i) + 1];
-            st_pop<0>(Aw + (int64_t)i * p.ps + t, Storage<S>::store(d[i]));
+            st_pop<0>(Aw + (int64_t)i * p.ps + t, R.one(d[i], key, cell, i));
         }
     }
 }

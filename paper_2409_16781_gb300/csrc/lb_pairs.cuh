@@ -86,7 +86,7 @@ __device__ __forceinline__ void bounce_fix_x2(const S* __restrict__ A, const uin
 // comes from the previous lane's second cell and the value at x0+2 (c_x =
 // -1) from the next lane's first cell when that lane holds the same row;
 // otherwise (warp edge, row edge, periodic wrap) the lane loads it itself.
-template <class S, bool FORCE, int HINT, bool MASK_FIRST = false>
+template <class S, bool FORCE, int HINT, bool MASK_FIRST = false, bool SR = false>
 __device__ __forceinline__ void pair_x2_update(const S* __restrict__ A, S* __restrict__ B,
                                                const uint8_t* __restrict__ code, const LatticeParams& p, int x0,
                                                int y, int z, int cell0, int lane, bool active) {
@@ -122,15 +122,22 @@ __device__ __forceinline__ void pair_x2_update(const S* __restrict__ A, S* __res
     bounce_fix_x2<S, HINT, FORM_AB, MASK_FIRST>(A, code, p, x0, y, z, cell0, c0, c1, d);
     relax_dev<f32x2, FORCE>(d, p);
     const bool f0 = !(c0 & CODE_TYPE), f1 = !(c1 & CODE_TYPE);
+    const Rounder<S, SR> R(p.sr_seed);
+    const uint32_t key = R.key(cell0);
     if (f0 && f1) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i)
-            st_pop<HINT>(reinterpret_cast<V*>(B + (int64_t)i * p.ps + cell0), pack2<S>(d[i].v.x, d[i].v.y));
+        for (int i = 0; i < Q; ++i) {
+            if constexpr (SR)
+                st_pop<HINT>(reinterpret_cast<uint32_t*>(B + (int64_t)i * p.ps + cell0),
+                             R.two(d[i].v.x, d[i].v.y, key, i));
+            else
+                st_pop<HINT>(reinterpret_cast<V*>(B + (int64_t)i * p.ps + cell0), pack2<S>(d[i].v.x, d[i].v.y));
+        }
     } else {  // solid cells are never written
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            if (f0) st_pop<HINT>(B + (int64_t)i * p.ps + cell0, Storage<S>::store(d[i].v.x));
-            if (f1) st_pop<HINT>(B + (int64_t)i * p.ps + cell0 + 1, Storage<S>::store(d[i].v.y));
+            if (f0) st_pop<HINT>(B + (int64_t)i * p.ps + cell0, R.one(d[i].v.x, key, cell0, i));
+            if (f1) st_pop<HINT>(B + (int64_t)i * p.ps + cell0 + 1, R.one(d[i].v.y, key, cell0 + 1, i));
         }
     }
 }

@@ -29,7 +29,7 @@ namespace lbgb {
 // Variants 1-3 (and 16 with MASK_FIRST: cells next to a wall gather their
 // neighbour codes before any value, blocks of at most 128 threads capped at
 // 48 registers).
-template <class S, bool FORCE, int HINT, bool MASK_FIRST = false>
+template <class S, bool FORCE, int HINT, bool MASK_FIRST = false, bool SR = false>
 __global__ void __launch_bounds__(MASK_FIRST ? 128 : 512, MASK_FIRST ? 10 : 0)
     step_kernel_rows(const S* __restrict__ A, S* __restrict__ B, const uint8_t* __restrict__ code, LatticeParams p,
                      int xblocks) {
@@ -46,8 +46,10 @@ __global__ void __launch_bounds__(MASK_FIRST ? 128 : 512, MASK_FIRST ? 10 : 0)
     M d[Q];
     pull_cell<S, HINT, FORM_AB, MASK_FIRST>(A, code, p, x, y, z, cell, cc, d);
     relax_dev<M, FORCE>(d, p);
+    const Rounder<S, SR> R(p.sr_seed);
+    const uint32_t key = R.key(cell);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) st_pop<HINT>(B + (int64_t)i * p.ps + cell, Storage<S>::store(d[i]));
+    for (int i = 0; i < Q; ++i) st_pop<HINT>(B + (int64_t)i * p.ps + cell, R.one(d[i], key, cell, i));
 }
 
 // ---------------------------------------------------------------------------
@@ -391,7 +393,7 @@ static cudaError_t step_quads16_t(const void* A, void* B, const uint8_t* code, c
 // Cells next to a wall leave the packed form for the bounce-back fix-up of
 // each cell and re-enter it.
 // ---------------------------------------------------------------------------
-template <class S, bool FORCE, int HINT, int MINB, bool MASK_FIRST = false>
+template <class S, bool FORCE, int HINT, int MINB, bool MASK_FIRST = false, bool SR = false>
 __global__ void __launch_bounds__(256 / MINB, MINB == 1 ? 0 : 4 * MINB)
     step_kernel_pairs_x2(const S* __restrict__ A, S* __restrict__ B, const uint8_t* __restrict__ code, LatticeParams p,
                          int xblocks) {
@@ -400,11 +402,11 @@ __global__ void __launch_bounds__(256 / MINB, MINB == 1 ? 0 : 4 * MINB)
     const int x0 = 2 * (xb * blockDim.x + threadIdx.x);
     const bool active = x0 < p.nx;
     const int xa = active ? x0 : 0;  // in-bounds address for idle lanes
-    pair_x2_update<S, FORCE, HINT, MASK_FIRST>(A, B, code, p, xa, row % p.ny, row / p.ny, xa + p.nx * row,
-                                               threadIdx.x & 31, active);
+    pair_x2_update<S, FORCE, HINT, MASK_FIRST, SR>(A, B, code, p, xa, row % p.ny, row / p.ny, xa + p.nx * row,
+                                                   threadIdx.x & 31, active);
 }
 
-template <class S, int HINT, int MINB, bool MASK_FIRST = false>
+template <class S, int HINT, int MINB, bool MASK_FIRST = false, bool SR = false>
 static cudaError_t step_pairs_x2_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p, int block,
                                    cudaStream_t st) {
     int bx = block > 0 ? (block / 32) * 32 : 64;  // whole warps (the shuffles need all 32 lanes)
@@ -417,10 +419,10 @@ static cudaError_t step_pairs_x2_t(const void* A, void* B, const uint8_t* code, 
     const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if (force)
-        step_kernel_pairs_x2<S, true, HINT, MINB, MASK_FIRST>
+        step_kernel_pairs_x2<S, true, HINT, MINB, MASK_FIRST, SR>
             <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     else
-        step_kernel_pairs_x2<S, false, HINT, MINB, MASK_FIRST>
+        step_kernel_pairs_x2<S, false, HINT, MINB, MASK_FIRST, SR>
             <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     return cudaGetLastError();
 }
@@ -512,7 +514,7 @@ static cudaError_t step_quads16_x2_t(const void* A, void* B, const uint8_t* code
     return cudaGetLastError();
 }
 
-template <class S, int HINT, bool MASK_FIRST = false>
+template <class S, int HINT, bool MASK_FIRST = false, bool SR = false>
 static cudaError_t step_rows_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p, int block,
                                cudaStream_t st);
 
@@ -831,7 +833,7 @@ static cudaError_t step_tma16_t(const void* A, void* B, const uint8_t* code, con
     return force ? launch_tma16<S, true, G>(A, B, code, p, g, st) : launch_tma16<S, false, G>(A, B, code, p, g, st);
 }
 
-template <class S, int HINT, bool MASK_FIRST>
+template <class S, int HINT, bool MASK_FIRST, bool SR>
 static cudaError_t step_rows_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p, int block,
                                cudaStream_t st) {
     int bx = block > 0 ? (block / 32) * 32 : 256;
@@ -844,15 +846,47 @@ static cudaError_t step_rows_t(const void* A, void* B, const uint8_t* code, cons
     const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if (force)
-        step_kernel_rows<S, true, HINT, MASK_FIRST><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+        step_kernel_rows<S, true, HINT, MASK_FIRST, SR>
+            <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     else
-        step_kernel_rows<S, false, HINT, MASK_FIRST><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+        step_kernel_rows<S, false, HINT, MASK_FIRST, SR>
+            <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     return cudaGetLastError();
+}
+
+// Stochastic rounding (16-bit storage, p.sr): the one-cell kernels (1-3, and
+// 16 with the mask-first bounce-back) and the packed two-cell kernels (13,
+// 15, 17) have a stochastically rounding form; every other variant runs 15
+// (or 1 where the two-cell kernels do not apply).
+template <class S>
+static cudaError_t step_sr_t(int variant, const void* A, void* B, const uint8_t* code, const LatticeParams& p,
+                             int block, cudaStream_t st) {
+    const bool pairs_ok = (p.nx % 2) == 0;
+    switch (variant) {
+        case 1: return step_rows_t<S, 0, false, true>(A, B, code, p, block, st);
+        case 2: return step_rows_t<S, 1, false, true>(A, B, code, p, block, st);
+        case 3: return step_rows_t<S, 2, false, true>(A, B, code, p, block, st);
+        case 16: return step_rows_t<S, 0, true, true>(A, B, code, p, block, st);
+        case 13:
+            if (pairs_ok) return step_pairs_x2_t<S, 0, 1, false, true>(A, B, code, p, block, st);
+            return step_rows_t<S, 0, false, true>(A, B, code, p, block, st);
+        case 17:
+            if (pairs_ok) return step_pairs_x2_t<S, 0, 2, true, true>(A, B, code, p, block, st);
+            return step_rows_t<S, 0, false, true>(A, B, code, p, block, st);
+        default:
+            if (pairs_ok)
+                return step_pairs_x2_t<S, 0, 2, false, true>(A, B, code, p, variant == 15 || block > 0 ? block : 64,
+                                                             st);
+            return step_rows_t<S, 0, false, true>(A, B, code, p, block > 0 ? block : 64, st);
+    }
 }
 
 template <class S>
 static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* code, const LatticeParams& p,
                           int block, cudaStream_t st) {
+    if constexpr (sizeof(S) == 2) {
+        if (p.sr) return step_sr_t<S>(variant, A, B, code, p, block, st);
+    }
     // the two-cell FP32/FP64 kernels have no FP32-storage/FP64-math form
     const bool pairs_ok = (p.nx % 2) == 0 && !std::is_same<S, f32d>::value;
     switch (variant) {

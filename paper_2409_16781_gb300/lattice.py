@@ -29,8 +29,11 @@ def velocity_set():
     return c.reshape(19, 3).astype(np.int64), w
 
 
+ROUNDING = {"nearest": 0, "stochastic": 1}
+
+
 def make_options(storage="f32", force=(0.0, 0.0, 0.0), stream=None, kernel=0, block=0, trt_magic=0.0,
-                 inplace=False):
+                 inplace=False, halo_z=False, rounding="nearest"):
     o = L.LbOptions()
     L.lib().lb_default_options(ctypes.byref(o))
     o.storage = L.STORAGE[storage] if isinstance(storage, str) else int(storage)
@@ -38,6 +41,8 @@ def make_options(storage="f32", force=(0.0, 0.0, 0.0), stream=None, kernel=0, bl
     o.block = int(block)
     o.trt_magic = float(trt_magic)
     o.inplace = 1 if inplace else 0
+    o.halo_z = 1 if halo_z else 0
+    o.rounding = ROUNDING[rounding] if isinstance(rounding, str) else int(rounding)
     for a in range(3):
         o.force[a] = float(force[a])
     o.stream = stream
@@ -49,17 +54,20 @@ def bytes_required(nx, ny, nz, storage="f32", inplace=False) -> int:
     return int(L.lib().lb_bytes_required(int(nx), int(ny), int(nz), ctypes.byref(o)))
 
 
-def autotune_key(device_name, storage, dims, force, flags, trt_magic=0.0, inplace=False) -> str:
+def autotune_key(device_name, storage, dims, force, flags, trt_magic=0.0, inplace=False,
+                 rounding="nearest") -> str:
     """The autotune cache key: GPU, storage, dims, forcing, geometry (a digest
-    of the flags, or "nowalls" when every cell is fluid), collision and
-    population layout -- everything the fastest step kernel depends on."""
+    of the flags, or "nowalls" when every cell is fluid), collision,
+    population layout and rounding -- everything the fastest step kernel
+    depends on."""
     import hashlib
     fl = None if flags is None else np.ascontiguousarray(flags, dtype=np.uint8)
     geo = ("walls:" + hashlib.blake2b(fl.tobytes(), digest_size=8).hexdigest()
            if fl is not None and fl.any() else "nowalls")
     nx, ny, nz = dims
     return "|".join([str(device_name), str(storage), f"{nx}x{ny}x{nz}", "force" if force else "noforce", geo]
-                    + (["trt"] if trt_magic else []) + (["inplace"] if inplace else []))
+                    + (["trt"] if trt_magic else []) + (["inplace"] if inplace else [])
+                    + (["sr"] if rounding in ("stochastic", 1) else []))
 
 
 class Lattice:
@@ -71,11 +79,15 @@ class Lattice:
     trt_magic: 0 = BGK collision; > 0 = two-relaxation-time collision with
     that magic parameter (lb_options.trt_magic).
     inplace: one population array updated in place (lb_options.inplace).
+    halo_z: a z-slab of a decomposed lattice, planes 0 and nz-1 being ghost
+    planes (lb_options.halo_z; see halo_pack / halo_unpack and slab.py).
+    rounding: "nearest" (default) or "stochastic" for 16-bit storage
+    (lb_options.rounding).
     """
 
     def __init__(self, nx, ny, nz, tau, u_lid=(0.0, 0.0, 0.0), flags=None, storage="f32",
                  force=(0.0, 0.0, 0.0), device=None, stream=None, kernel=0, block=0,
-                 library_memory=False, trt_magic=0.0, inplace=False):
+                 library_memory=False, trt_magic=0.0, inplace=False, halo_z=False, rounding="nearest"):
         import torch
 
         self.lib = L.lib()
@@ -90,7 +102,9 @@ class Lattice:
             stream = torch.cuda.current_stream(self.device)
         self.stream = stream
         opts = make_options(storage, force, ctypes.c_void_p(stream.cuda_stream), kernel, block, trt_magic,
-                            inplace)
+                            inplace, halo_z, rounding)
+        self.halo_z = bool(halo_z)
+        self.rounding = rounding
         self.trt_magic = float(trt_magic)
         self.inplace = bool(inplace)
         ulid = (ctypes.c_double * 3)(*[float(v) for v in u_lid])
@@ -223,6 +237,20 @@ class Lattice:
                 "lb_get_populations_at")
         return out
 
+    def halo_bytes(self) -> int:
+        """Bytes of one halo message (lb_halo_bytes; 0 without ghost planes)."""
+        return int(self.lib.lb_halo_bytes(self._h))
+
+    def halo_pack(self, send_lo, send_hi):
+        """lb_halo_pack into two device tensors of halo_bytes() bytes each."""
+        L.check(self.lib.lb_halo_pack(self._h, ctypes.c_void_p(send_lo.data_ptr()),
+                                      ctypes.c_void_p(send_hi.data_ptr())), "lb_halo_pack")
+
+    def halo_unpack(self, recv_lo, recv_hi):
+        """lb_halo_unpack from two device tensors of halo_bytes() bytes each."""
+        L.check(self.lib.lb_halo_unpack(self._h, ctypes.c_void_p(recv_lo.data_ptr()),
+                                        ctypes.c_void_p(recv_hi.data_ptr())), "lb_halo_unpack")
+
     def set_kernel(self, variant: int, block: int = 0):
         L.check(self.lib.lb_set_kernel(self._h, int(variant), int(block)), "lb_set_kernel")
 
@@ -235,7 +263,7 @@ class Lattice:
         Returns (variant, block, ms/step)."""
         import torch
         key = autotune_key(torch.cuda.get_device_name(self.device), self.storage, (self.nx, self.ny, self.nz),
-                           self._force, self._flags, self.trt_magic, self.inplace)
+                           self._force, self._flags, self.trt_magic, self.inplace, self.rounding)
         path = os.environ.get("LBGB_AUTOTUNE_CACHE",
                               os.path.join(os.path.expanduser("~"), ".cache", "lbgb", "autotune.json"))
         table = {}

@@ -256,6 +256,11 @@ class Scheduler:
         return stats
 
 
+def _rounding_for(storage: str, rounding: str) -> str:
+    """Stochastic rounding applies to 16-bit storage only."""
+    return rounding if storage in ("f16s", "bf16s") else "nearest"
+
+
 def _checksum(u):
     return float(np.sqrt(np.mean(np.sum(u * u, axis=0))))
 
@@ -279,17 +284,18 @@ class BatchBackend:
     results come back asynchronously (lb_batch_fetch) into pinned buffers."""
 
     def __init__(self, capacity_bytes: int, max_slots: int = 1024, device=None, keep_fields: bool = False,
-                 inplace: bool = False):
+                 inplace: bool = False, rounding: str = "nearest"):
         from .batch import Batch
         self.batch = Batch(capacity_bytes, max_slots=max_slots, device=device)
         self.keep = keep_fields
         self.inplace = inplace  # one population array per slot: about twice the requests per budget
+        self.rounding = rounding  # of 16-bit requests (lb_options.rounding)
         self.pending = {}
 
     def admit(self, req):
         return self.batch.try_add(req.nx, req.ny, req.nz, req.tau, req.steps, u_lid=req.u_lid,
                                   flags=req.flags(), storage=req.storage, force=req.force,
-                                  inplace=self.inplace)
+                                  inplace=self.inplace, rounding=_rounding_for(req.storage, self.rounding))
 
     def step(self, n):
         self.batch.step(n)
@@ -327,8 +333,9 @@ class SequentialBackend:
 
     whole_requests = True
 
-    def __init__(self, storage: str = "f32", device=None, keep_fields: bool = False):
+    def __init__(self, storage: str = "f32", device=None, keep_fields: bool = False, rounding: str = "nearest"):
         self.storage = storage
+        self.rounding = rounding
         self.device = device
         self.keep = keep_fields
         self.lat = None
@@ -341,7 +348,8 @@ class SequentialBackend:
             return None
         from .lattice import Lattice
         self.lat = Lattice(req.nx, req.ny, req.nz, req.tau, u_lid=req.u_lid, flags=req.flags(),
-                           storage=self.storage, force=req.force, device=self.device)
+                           storage=self.storage, force=req.force, device=self.device,
+                           rounding=_rounding_for(self.storage, self.rounding))
         self.left = req.steps
         self.key += 1
         return self.key

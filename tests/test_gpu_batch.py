@@ -178,26 +178,97 @@ def test_admission_limits():
     b.close()
 
 
+def _same_fields_as_alone(results, reqs):
+    """Each served request's rho and u against the same request run alone
+    by the one-at-a-time baseline (same storage), element by element over
+    its fluid cells."""
+    got = {r.rid: r.fields for r in results}
+    for req in reqs:
+        st1 = serve([req], SequentialBackend(storage=req.storage, keep_fields=True))
+        rho_a, u_a = st1.results[0].fields
+        rho_b, u_b = got[req.rid]
+        mask = req.flags() == 0
+        tol = VEL_TOL[req.storage]
+        assert vel_err(u_b, u_a, mask) <= tol, (req.rid, req.storage)
+        assert np.abs(rho_b[mask] - rho_a[mask]).max() <= tol * np.abs(rho_a[mask]).max(), req.rid
+        assert np.abs(u_a[:, mask]).max() > 0
+
+
 @pytest.mark.parametrize("policy", ["fifo", "srpt"])
 def test_serve_end_to_end_same_as_sequential(policy):
     """A small request stream through the batched server and through the
-    one-at-a-time baseline (same storage per request) gives the same
-    velocity fields (checksums), and every request completes."""
+    one-at-a-time baseline (same storage per request) gives the same rho and
+    u fields element by element, and every request completes."""
     reqs = W.request_stream(n=10, rate_hz=200.0, seed=5, min_cells=6 ** 3, max_cells=20 ** 3,
                             steps_range=(20, 120))
     be = BatchBackend(capacity_bytes=128 << 20, max_slots=8, keep_fields=True)
     st = serve(reqs, be, chunk_ms=2.0, policy=policy, target_cells=5000)
     be.close()
     assert len(st.results) == len(reqs) and not st.rejected
-    got = {r.rid: r.checksum for r in st.results}
-    for req in reqs:
-        seq = SequentialBackend(storage=req.storage, keep_fields=True)
-        st1 = serve([req], seq)
-        ref = st1.results[0].checksum
-        tol = 1e-5 if req.storage == "f32" else 2e-3
-        assert abs(got[req.rid] - ref) <= tol * max(ref, 1e-12) + 1e-12
+    _same_fields_as_alone(st.results, reqs)
     s = st.summary()
     assert s["requests"] == len(reqs) and s["p99_s"] >= s["p50_s"]
+
+
+class _CountingBackend(BatchBackend):
+    """Records every positive quota the scheduler grants: per request, the
+    list of (chunk number, quota)."""
+
+    def __init__(self, *a, **kw):
+        super().__init__(*a, **kw)
+        self.grants = {}
+        self.slot_rid = {}
+        self.chunk = 0
+
+    def admit(self, req):
+        h = super().admit(req)
+        if h is not None:
+            self.slot_rid[h] = req.rid
+            self.grants[req.rid] = []
+        return h
+
+    def set_quotas(self, quotas):
+        for h, q in quotas.items():
+            if q > 0:
+                self.grants[self.slot_rid[h]].append((self.chunk, int(q)))
+        super().set_quotas(quotas)
+
+    def step(self, n):
+        super().step(n)
+        self.chunk += 1
+
+
+@pytest.mark.parametrize("rounding", ["nearest", "stochastic"])
+def test_serve_chunked_quotas_and_pauses_same_as_alone(rounding):
+    """Through serve() with the srpt policy: every request is granted its
+    steps in at least 3 chunks (max_chunk caps a chunk), some requests are
+    paused (quota 0) between grants while others run, and each result
+    equals the request run alone element by element."""
+    reqs = W.request_stream(n=12, rate_hz=400.0, seed=7, min_cells=6 ** 3, max_cells=18 ** 3,
+                            steps_range=(60, 160))
+    be = _CountingBackend(capacity_bytes=128 << 20, max_slots=12, keep_fields=True, rounding=rounding)
+    st = serve(reqs, be, chunk_ms=1.0, policy="srpt", target_cells=3000, max_chunk=16, min_chunk=4)
+    be.close()
+    assert len(st.results) == len(reqs) and not st.rejected
+    paused_between = 0
+    for req in reqs:
+        g = be.grants[req.rid]
+        chunks = [c for c, _ in g]
+        assert sum(q for _, q in g) == req.steps
+        assert len(g) >= 3, (req.rid, g)
+        if chunks[-1] - chunks[0] + 1 > len(chunks):  # chunks ran without it in between
+            paused_between += 1
+    assert paused_between > 0
+    if rounding == "nearest":
+        _same_fields_as_alone(st.results, reqs)
+    else:
+        got = {r.rid: r.fields for r in st.results}
+        for req in reqs:  # the same request alone, with the same rounding
+            st1 = serve([req], SequentialBackend(storage=req.storage, keep_fields=True, rounding=rounding))
+            rho_a, u_a = st1.results[0].fields
+            rho_b, u_b = got[req.rid]
+            mask = req.flags() == 0
+            assert np.array_equal(u_b[:, mask], u_a[:, mask]) and np.array_equal(rho_b[mask], rho_a[mask])
 
 
 def test_step_quotas():
@@ -295,9 +366,4 @@ def test_serve_inplace_same_as_sequential():
     st = serve(reqs, be, chunk_ms=2.0, policy="srpt", target_cells=5000)
     be.close()
     assert len(st.results) == len(reqs) and not st.rejected
-    got = {r.rid: r.checksum for r in st.results}
-    for req in reqs:
-        st1 = serve([req], SequentialBackend(storage=req.storage, keep_fields=True))
-        ref = st1.results[0].checksum
-        tol = 1e-5 if req.storage == "f32" else 2e-3
-        assert abs(got[req.rid] - ref) <= tol * max(ref, 1e-12) + 1e-12
+    _same_fields_as_alone(st.results, reqs)
