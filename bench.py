@@ -10,9 +10,18 @@ reduction used as the divergence check.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 runs under torchrun, one rank per GPU; the lattice update does not
-shard here (replicas: every rank advances its own lattice, no collective on
-the data path) and value = all ranks' cell updates / max-over-ranks time.
+N > 1 runs under torchrun, one rank per GPU.  By default the lattice is
+decomposed into z-slabs (--decomp slab): rank r owns 256 z-planes of one
+256 x 256 x (256 N) Taylor-Green lattice (weak scaling) and trades the five
+c_z = +-1 populations of its boundary planes with its z-neighbours after
+every step (NCCL send/recv); --decomp replicas runs an independent lattice
+per rank instead.  value = all ranks' cell updates / max-over-ranks time.
+
+Besides the headline line's TGV measurement, the default run measures the
+other configurations (``configs``): the 512^3 porous channel in FP32 and
+shifted FP16, the 768^3 cavity precision study (5000 steps, three tau), and
+the 2000-request serving stream at 0.5x and 2x the sequential FP32
+capacity; --no-configs skips them.
 
 The reference arm (--impl reference) times the FP64 CPU oracle on the host
 cores, each step a bounded sample (a z-slab of the same lattice).
@@ -35,7 +44,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "D3Q19 MLUPS & fraction of HBM roofline; batched-serve p50/p99 vs plain FP32 launches"
-STORAGE_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2, "f32d": 4}
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2, "f32d": 4, "e3m12s": 2}
 FALLBACK_HBM_GBS = 6800.0
 # the files that make up the step kernel (hashed to tie ncu figures to it)
 STEP_SOURCES = ("lb_common.cuh", "lb_fpconv.cuh", "lb_internal.h", "lb_kernels.cuh", "lb_pairs.cuh", "lb_mbarrier.cuh",
@@ -88,6 +97,13 @@ def parse_args(argv=None):
                     help="path prefix for per-request JSON-lines records of the serving runs")
     ap.add_argument("--serve-tight-gb", type=float, default=0.75,
                     help="HBM budget of the memory-bound serving comparison (two arrays vs in place; 0 = skip)")
+    ap.add_argument("--serve-rounding", choices=["nearest", "stochastic"], default="stochastic",
+                    help="rounding of the 16-bit requests' stored values in the batched server")
+    ap.add_argument("--decomp", choices=["slab", "replicas"], default="slab",
+                    help="N > 1: z-slabs of one lattice with a halo exchange (default), or replicas")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the porous 512^3, cavity 768^3 precision and 2000-request serving sections")
+    ap.add_argument("--precision-steps", type=int, default=5000, help="steps of the 768^3 precision study")
     return ap.parse_args(argv)
 
 
@@ -100,6 +116,7 @@ class Dist:
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
         self.pg = False
+        self.backend = None
         if self.world > 1:
             import torch.distributed as dist
             if backend is None:
@@ -317,6 +334,22 @@ def tgv_inputs(n):
     return W.taylor_green_fields(n, n, n, u0=0.05)
 
 
+def tgv_slab_inputs(n, nz, z0, z1, u0=0.05):
+    """Taylor-Green fields of an n x n x nz lattice (wavenumber 2 pi / edge
+    on each axis) on planes z0-1 .. z1 (periodic): a z-slab with its ghost
+    planes, without building the whole lattice's fields."""
+    import numpy as np
+    kx = ky = 2 * math.pi / n
+    kz = 2 * math.pi / nz
+    x = np.arange(n)[None, None, :]
+    y = np.arange(n)[None, :, None]
+    z = np.array([(z0 - 1) % nz] + list(range(z0, z1)) + [z1 % nz])[:, None, None]
+    u = np.zeros((3, len(z), n, n))
+    u[0] = u0 * np.sin(kx * x) * np.cos(ky * y) * np.cos(kz * z)
+    u[1] = -u0 * np.cos(kx * x) * np.sin(ky * y) * np.cos(kz * z)
+    return np.ones((len(z), n, n)), u
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args, dist: Dist):
     import numpy as np
@@ -327,21 +360,46 @@ def run_ours(args, dist: Dist):
     dev = torch.device("cuda", dist.local_rank)
     torch.cuda.set_device(dev)
     n = args.n
-    N = n ** 3
+    N = n ** 3           # cells this rank updates per step
     tau = 0.55
     stream = torch.cuda.current_stream(dev)
-    rho0, u0 = tgv_inputs(n)
-    lat = Lattice(n, n, n, tau, storage=args.storage, device=dev, stream=stream,
-                  kernel=args.kernel, block=args.block, inplace=args.inplace, trt_magic=args.trt_magic)
-    lat.init_fields(rho0, u0)
+    slab = None
+    if dist.world > 1 and args.decomp == "slab":
+        # z-slabs of one n x n x (n * world) lattice, n own planes per rank
+        from paper_2409_16781_gb300.slab import SlabExchange, SlabLattice
+        if args.inplace:
+            raise SystemExit("--decomp slab needs two population arrays (no --inplace)")
+        nzg = n * dist.world
+        slab = SlabLattice(n, n, nzg, tau, storage=args.storage, rank=dist.rank, world=dist.world,
+                           exchange=SlabExchange(dist.rank, dist.world,
+                                                 device=dev if dist.backend == "nccl" else None),
+                           device=dev, stream=stream,
+                           kernel=args.kernel, block=args.block)
+        lat = slab.lattice
+        rho0, u0 = tgv_slab_inputs(n, nzg, slab.z0, slab.z1)
+        lat.init_fields(rho0, u0)
+        slab.halo()
+    else:
+        rho0, u0 = tgv_inputs(n)
+        lat = Lattice(n, n, n, tau, storage=args.storage, device=dev, stream=stream,
+                      kernel=args.kernel, block=args.block, inplace=args.inplace, trt_magic=args.trt_magic)
+        lat.init_fields(rho0, u0)
     tuned = None
     if args.kernel == 0 and not args.no_autotune:
         tuned = lat.autotune(reps=20, cache=False)
 
+    def step():
+        lat.step(1)
+        if slab is not None:
+            slab.halo()
+
+    def totals():
+        return slab.totals() if slab is not None else lat.totals()
+
     launches_per_check = 2  # reduction kernel + finalize kernel
     for _ in range(args.warmup):
-        lat.step(1)
-    lat.totals()
+        step()
+    totals()
     torch.cuda.synchronize(dev)
 
     K = args.steps
@@ -358,10 +416,12 @@ def run_ours(args, dist: Dist):
         ev[k][0].record(stream)
         lat.step(1)
         ev[k][1].record(stream)
+        if slab is not None:
+            slab.halo()
         if args.check_every > 0 and (k + 1) % args.check_every == 0 and k + 1 < K:
-            lat.totals()
+            totals()
             n_checks += 1
-    mass, mom = lat.totals()
+    mass, mom = totals()
     n_checks += 1
     t_end.record(stream)
     torch.cuda.synchronize(dev)
@@ -384,15 +444,22 @@ def run_ours(args, dist: Dist):
         dist.barrier()
         t0 = time.perf_counter()
         lat.lib.lb_init_fields(lat.handle, rho_h.data_ptr(), u_h.data_ptr())
-        lat.step(K)
+        if slab is None:
+            lat.step(K)
+        else:
+            slab.halo()
+            for _ in range(K):
+                step()
         st = lat.lib.lb_moments(lat.handle, rho_out.data_ptr(), u_out.data_ptr())
         t1 = time.perf_counter()
         assert st == 0
         dist.barrier()
         e2e_val, _ = aggregate_replicas(dist, N, K, t1 - t0)
+        moved = dist.sum(32 * rho_h.numel())  # rho + u, 8 + 24 bytes per cell, all ranks
         e2e = {"value": round(e2e_val, 1), "unit": "MLUPS",
-               "h2d_bytes_per_step": int(32 * N / K), "d2h_bytes_per_step": int(32 * N / K),
-               "what": "lb_init_fields(host rho,u) + lb_step(K) + lb_moments(host rho,u), pinned host buffers"}
+               "h2d_bytes_per_step": int(moved / K), "d2h_bytes_per_step": int(moved / K),
+               "what": "lb_init_fields(host rho,u) + lb_step(K) + lb_moments(host rho,u), pinned host buffers"
+                       + ("; z-slab halo exchange after every step" if slab is not None else "")}
 
     peak, peak_kind = measured_peaks()
     bpu = bytes_per_update(args.storage)
@@ -410,25 +477,26 @@ def run_ours(args, dist: Dist):
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": dist.world,
         "steps": K, "warmup": args.warmup, "ms_per_step": round(t_max * 1e3 / K, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"f64": "f64", "f32": "f32", "f16s": "f16", "bf16s": "bf16", "f32d": "f32+f64"}[args.storage],
+        "dtype": {"f64": "f64", "f32": "f32", "f16s": "f16", "bf16s": "bf16", "f32d": "f32+f64",
+                  "e3m12s": "e3m12"}[args.storage],
         "data": "synthetic",
-        "config": {"workload": f"taylor-green vortex {n}^3, D3Q19 BGK, {args.storage} populations "
-                               f"(f - w), tau={tau}, u0=0.05, k=2pi/{n}",
-                   "lattice": [n, n, n], "storage": args.storage, "tau": tau,
-                   "populations": "one array, in place (AA pattern)" if args.inplace else "two arrays (A -> B)",
-                   "collision": f"TRT, magic {args.trt_magic}" if args.trt_magic else "BGK",
-                   "check_every": args.check_every,
-                   "kernel": ({"variant": tuned[0], "block": tuned[1], "chosen_by": "lb_autotune"}
-                              if tuned else {"variant": args.kernel, "block": args.block,
-                                             "chosen_by": "command line"}),
-                   "l2": f"no flush: working set {2 * 19 * STORAGE_BYTES[args.storage] * N / 1e9:.2f} GB "
-                         "> 129 MB L2",
-                   "parallelism": "replicas" if dist.world > 1 else "single"},
+        "config": {**reference_config(args),
+                   "workload": (f"taylor-green vortex {n}^3, D3Q19 BGK, {args.storage} populations "
+                                f"(f - w), tau={tau}, u0=0.05, k=2pi/{n}") if slab is None else
+                               (f"taylor-green vortex {n}x{n}x{n * dist.world} in {dist.world} z-slabs of "
+                                f"{n}^3, D3Q19 BGK, {args.storage} populations (f - w), tau={tau}, u0=0.05"),
+                   "lattice": [n, n, n * (dist.world if slab is not None else 1)],
+                   "parallelism": ("single" if dist.world == 1 else
+                                   "replicas" if slab is None else
+                                   f"z-slabs over {dist.world} GPUs, halo exchange by NCCL send/recv")},
+        "kernel": ({"variant": tuned[0], "block": tuned[1], "chosen_by": "lb_autotune"}
+                   if tuned else {"variant": args.kernel, "block": args.block, "chosen_by": "command line"}),
         "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": K + launches_per_check * n_checks,
+        # step launches, 2 per FP64 check; z-slabs: + halo pack and unpack per step
+        "gpu_launches": K + launches_per_check * n_checks + (2 * K if slab is not None else 0),
         "clocks": clock_summary,
-        "mass_drift_rel": abs(mass - N) / N,
+        "mass_drift_rel": abs(mass - N * dist.world) / (N * dist.world) if slab is not None else abs(mass - N) / N,
     }
     lat.close()
     return line
@@ -446,12 +514,14 @@ def forms_section(n, steps=200, device=None):
     peak, peak_kind = measured_peaks()
     rho0, u0 = tgv_inputs(n)
     out = []
-    for storage, inplace, trt in (("f16s", False, 0.0), ("bf16s", False, 0.0), ("f64", False, 0.0),
-                                  ("f32d", False, 0.0), ("f32", False, 3 / 16), ("f32", True, 0.0),
-                                  ("f16s", True, 0.0)):
+    for storage, inplace, trt, rounding in (("f16s", False, 0.0, "nearest"), ("f16s", False, 0.0, "stochastic"),
+                                            ("bf16s", False, 0.0, "nearest"), ("f64", False, 0.0, "nearest"),
+                                            ("f32d", False, 0.0, "nearest"), ("f32", False, 3 / 16, "nearest"),
+                                            ("f32", True, 0.0, "nearest"), ("f16s", True, 0.0, "nearest"),
+                                            ("e3m12s", False, 0.0, "stochastic")):
         stream = torch.cuda.current_stream(device)
         lat = Lattice(n, n, n, 0.55, storage=storage, stream=stream, device=device, inplace=inplace,
-                      trt_magic=trt)
+                      trt_magic=trt, rounding=rounding)
         lat.init_fields(rho0, u0)
         v, b, _ = lat.autotune(reps=10, cache=False)
         k = steps if STORAGE_BYTES[storage] <= 4 and storage != "f32d" else steps // 4
@@ -466,7 +536,8 @@ def forms_section(n, steps=200, device=None):
         glups = n ** 3 / ms / 1e6
         gbs = glups * bytes_per_update(storage)
         out.append({"storage": storage, "populations": "in place" if inplace else "two arrays",
-                    "collision": "TRT 3/16" if trt else "BGK", "variant": v, "block": b, "steps": k,
+                    "collision": "TRT 3/16" if trt else "BGK", "rounding": rounding,
+                    "variant": v, "block": b, "steps": k,
                     "glups": round(glups, 2), "gbs": round(gbs, 1),
                     "frac": round(gbs / peak, 4), "peak_kind": peak_kind,
                     "bytes_per_update": bytes_per_update(storage)})
@@ -479,12 +550,16 @@ def forms_section(n, steps=200, device=None):
 
 # ---------------------------------------------------------------- serving
 def run_serving(n_requests, rate_multipliers=(2.0,), budget_gb=64.0, seed=16781, calib=16,
-                device=None, tight_budget_gb=0.75, max_wait_s=60.0, log_prefix=None):
+                device=None, tight_budget_gb=0.75, max_wait_s=60.0, log_prefix=None, rounding="stochastic",
+                accuracy_every=1):
     """Continuous-batching serving of a seeded Poisson stream of cavity /
     channel requests (sizes log-uniform 16^3..192^3, aspect <= 4, tau in
-    [0.52, 1], steps in [200, 5000], FP32 / shifted-FP16 50/50), against the
-    same stream served one plain FP32 lattice at a time.  Arrival rates are
-    set as multiples of the measured sequential FP32 capacity."""
+    [0.52, 1], steps in [200, 5000], FP32 / shifted-FP16 50/50, the FP16
+    requests' stored values rounded as `rounding`), against the same stream
+    served one plain FP32 lattice at a time.  Arrival rates are set as
+    multiples of the measured sequential FP32 capacity.  The velocity error
+    of the FP16 requests (every `accuracy_every`-th of them) against FP32 is
+    in f16s_accuracy."""
     import torch
 
     from paper_2409_16781_gb300 import workloads as W
@@ -498,16 +573,19 @@ def run_serving(n_requests, rate_multipliers=(2.0,), budget_gb=64.0, seed=16781,
     st = serve(cal, SequentialBackend("f32", device=device))
     capacity = len(cal) / max(st.makespan, 1e-9)      # requests per second
     out = {"requests": n_requests, "capacity_req_per_s": round(capacity, 3),
-           "hbm_budget_gb": budget_gb, "storage_mix": "f32/f16s 50/50 (batched); f32 (sequential)",
+           "hbm_budget_gb": budget_gb,
+           "storage_mix": f"f32/f16s 50/50, f16s rounded {rounding}; f16s requests whose predicted "
+                          "deviations are below 2^-13 served in f32 (batched); f32 (sequential)",
            "policy": "batched: shortest remaining work first"
                      + (f", requests waiting over {max_wait_s:g} s first (oldest first)" if max_wait_s else "")
                      + ", 4M-cell occupancy target, 8 ms chunks, 3 queued; sequential: FIFO, one lattice "
                        "at a time, one launch per step",
            "runs": []}
-    out["f16s_accuracy"] = f16s_accuracy(base, samples=6, device=device)
+    out["f16s_accuracy"] = f16s_accuracy(base, every=accuracy_every, device=device, rounding=rounding)
     for mult in rate_multipliers:
         reqs = W.request_stream(n=n_requests, rate_hz=mult * capacity, seed=seed)
-        be = BatchBackend(int(budget_gb * (1 << 30)), max_slots=1024, device=device)
+        be = BatchBackend(int(budget_gb * (1 << 30)), max_slots=1024, device=device, rounding=rounding,
+                          promote=True)
         sb = serve(reqs, be, policy="srpt", target_cells=4_000_000, max_wait_s=max_wait_s)
         be.close()
         torch.cuda.synchronize()
@@ -526,7 +604,8 @@ def run_serving(n_requests, rate_multipliers=(2.0,), budget_gb=64.0, seed=16781,
         reqs = W.request_stream(n=n_requests, rate_hz=mult * capacity, seed=seed)
         tight = {"budget_gb": tight_budget_gb, "rate_multiplier": mult}
         for name, inplace in (("two_arrays", False), ("in_place", True)):
-            be = BatchBackend(int(tight_budget_gb * (1 << 30)), max_slots=1024, device=device, inplace=inplace)
+            be = BatchBackend(int(tight_budget_gb * (1 << 30)), max_slots=1024, device=device, inplace=inplace,
+                              rounding=rounding, promote=True)
             st = serve(reqs, be, policy="srpt", target_cells=4_000_000, max_wait_s=max_wait_s)
             be.close()
             torch.cuda.synchronize()
@@ -535,31 +614,37 @@ def run_serving(n_requests, rate_multipliers=(2.0,), budget_gb=64.0, seed=16781,
     return out
 
 
-def f16s_accuracy(requests, samples=6, device=None):
-    """Velocity error of served FP16-storage requests: each sampled request
-    (the largest cells x steps first, then every other) runs alone in FP16S
-    and in FP32; max |u16 - u32| / max |u32| over fluid cells."""
+def f16s_accuracy(requests, every=1, device=None, rounding="stochastic"):
+    """Velocity error of the FP16-storage requests as the batched server
+    serves them: every `every`-th FP16 request (in request order) that the
+    storage policy keeps in FP16 runs alone in FP16S, rounded as the server
+    rounds it (a slot gives bitwise the lattice-alone result), and in FP32;
+    max |u16 - u32| / max |u32| over fluid cells.  Requests the policy
+    serves in FP32 are counted as promoted."""
     from paper_2409_16781_gb300 import Lattice
-    cand = sorted([r for r in requests if r.storage == "f16s"], key=lambda r: -r.cells * r.steps)
-    pick = cand[:samples // 2] + cand[samples // 2::max(1, len(cand) // max(1, samples - samples // 2))]
-    pick = pick[:samples]
+    from paper_2409_16781_gb300.serve import served_storage
+    sixteen = [r for r in requests if r.storage == "f16s"]
+    promoted = sum(served_storage(r) != "f16s" for r in sixteen)
+    pick = [r for r in sixteen if served_storage(r) == "f16s"][::max(1, int(every))]
     errs = []
     for r in pick:
         u = {}
-        for storage in ("f32", "f16s"):
+        for storage, rnd in (("f32", "nearest"), ("f16s", rounding)):
             lat = Lattice(r.nx, r.ny, r.nz, r.tau, u_lid=r.u_lid, flags=r.flags(), storage=storage,
-                          force=r.force, device=device)
+                          force=r.force, device=device, rounding=rnd)
             lat.step(r.steps)
             u[storage] = lat.moments()[1]
             lat.close()
         mask = r.flags() == 0
         ref = u["f32"][:, mask]
         errs.append(float(abs(u["f16s"][:, mask] - ref).max() / max(abs(ref).max(), 1e-30)))
-    return {"sampled": len(errs), "max_err": max(errs) if errs else None,
+    worst = sorted(zip(errs, pick), key=lambda t: -t[0])[:5]
+    return {"checked": len(errs), "of_f16s_requests": len(sixteen), "promoted_to_f32": promoted,
+            "rounding": rounding, "max_err": max(errs) if errs else None,
             "median_err": sorted(errs)[len(errs) // 2] if errs else None,
             "within_2e-3": sum(e <= 2e-3 for e in errs),
-            "cases": [{"dims": [r.nx, r.ny, r.nz], "tau": round(r.tau, 3), "steps": r.steps, "kind": r.kind,
-                       "err": e} for r, e in zip(pick, errs)]}
+            "worst": [{"rid": r.rid, "dims": [r.nx, r.ny, r.nz], "tau": round(r.tau, 3), "steps": r.steps,
+                       "kind": r.kind, "err": e} for e, r in worst]}
 
 
 # ---------------------------------------------------------------- oracle
@@ -609,6 +694,21 @@ def cpu_baseline(n, budget_s=12.0, single_budget_s=4.0):
     return out
 
 
+def reference_config(args):
+    """The `config` of our arm's line for the same arguments (N = 1), so that
+    the two arms' lines name the same workload."""
+    n, tau = args.n, 0.55
+    return {"workload": f"taylor-green vortex {n}^3, D3Q19 BGK, {args.storage} populations "
+                        f"(f - w), tau={tau}, u0=0.05, k=2pi/{n}",
+            "lattice": [n, n, n], "storage": args.storage, "tau": tau,
+            "populations": "one array, in place (AA pattern)" if args.inplace else "two arrays (A -> B)",
+            "collision": f"TRT, magic {args.trt_magic}" if args.trt_magic else "BGK",
+            "check_every": args.check_every,
+            "l2": f"no flush: working set {2 * 19 * STORAGE_BYTES[args.storage] * n ** 3 / 1e9:.2f} GB "
+                  "> 129 MB L2",
+            "parallelism": "single"}
+
+
 def run_reference(args, dist: Dist):
     n = args.n
     # calibrate: one step on an 8-plane slab, then size the per-step sample
@@ -638,8 +738,7 @@ def run_reference(args, dist: Dist):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total * 1e3 / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "impl": "reference",
-        "config": {"workload": f"taylor-green vortex {n}^3, D3Q19 BGK, tau=0.55, u0=0.05, k=2pi/{n}",
-                   "lattice": [n, n, n], "storage": args.storage, "parallelism": "single"},
+        "config": reference_config(args),
         "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": oracle_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
@@ -670,9 +769,11 @@ def main(argv=None):
         if dist.rank == 0 and dist.world == 1 and n_serve > 0:
             line["serving"] = run_serving(n_serve, (2.0,), args.serve_budget_gb,
                                           tight_budget_gb=args.serve_tight_gb,
-                                          max_wait_s=args.serve_max_wait or None)
+                                          max_wait_s=args.serve_max_wait or None, rounding=args.serve_rounding)
         elif dist.rank == 0:
             line["serving"] = None
+        if dist.rank == 0 and dist.world == 1 and not args.no_configs:
+            line["configs"] = configs_section(args)
         if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.n)
         elif dist.rank == 0:
@@ -684,10 +785,35 @@ def main(argv=None):
     return 0
 
 
-def porous_line(args):
-    """Porous channel 512^3, FP32, tau 0.8, g = 1e-6 x, walls on the y/z faces,
-    400 spheres (radius U[8,24], SplitMix64 seed 2409): MLUPS over all cells
-    and over fluid cells, CUDA events on the lattice's stream."""
+def configs_section(args):
+    """The other configurations of the workload list, measured in the
+    default run: porous channel 512^3 (FP32, and FP16 rounded
+    stochastically), the 768^3 cavity precision study, and the
+    2000-request serving stream at 0.5x and 2x the sequential FP32
+    capacity (p50 / p99 for both servers; the FP16 requests' error checked
+    on every tenth of them)."""
+    import torch
+    out = {}
+    t0 = time.time()
+    out["porous_512"] = porous_section()
+    torch.cuda.empty_cache()
+    out["cavity_768_precision"] = precision_section(args.precision_steps,
+                                                    tuple(float(t) for t in args.taus.split(",")))
+    torch.cuda.empty_cache()
+    out["serving_2000"] = run_serving(2000, (0.5, 2.0), args.serve_budget_gb, tight_budget_gb=0,
+                                      max_wait_s=args.serve_max_wait or None, rounding=args.serve_rounding,
+                                      accuracy_every=10)
+    out["wall_s"] = round(time.time() - t0, 1)
+    return out
+
+
+def porous_section(forms=(("f32", "nearest"), ("f16s", "stochastic")), steps=200, warmup=5):
+    """Porous channel 512^3, tau 0.8, g = 1e-6 x, walls on the y/z faces,
+    400 spheres (radius U[8,24], SplitMix64 seed 2409), in each storage
+    form: GLUPS over all cells and over fluid cells (CUDA events on the
+    lattice's stream around `steps` steps, autotuned kernel), the fraction of
+    the measured HBM bandwidth at the algorithmic bytes per update, and the
+    FP64 mass drift and momentum."""
     import torch
 
     from paper_2409_16781_gb300 import Lattice
@@ -695,35 +821,52 @@ def porous_line(args):
     n = 512
     flags = W.porous_flags(n, n, n, n_spheres=400, r_min=8, r_max=24, seed=2409)
     fluid = int((flags == 0).sum())
-    stream = torch.cuda.current_stream()
-    lat = Lattice(n, n, n, 0.8, flags=flags, storage=args.storage, force=(1e-6, 0.0, 0.0), stream=stream)
-    tuned = lat.autotune(reps=10, cache=False)
-    for _ in range(args.warmup):
-        lat.step(1)
-    m0, _ = lat.totals()
-    K = args.steps
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    lat.step(K)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    sec = e0.elapsed_time(e1) / 1e3
-    m1, p1 = lat.totals()
     N = n ** 3
-    bpu = bytes_per_update(args.storage)
     peak, kind = measured_peaks()
-    lat.close()
-    return {"metric": METRIC, "value": round(N * K / sec / 1e6, 1), "unit": "MLUPS", "n_gpus": 1, "steps": K,
-            "warmup": args.warmup, "ms_per_step": round(sec * 1e3 / K, 5), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+    stream = torch.cuda.current_stream()
+    out = {"lattice": [n, n, n], "solid_fraction": round(1 - fluid / N, 4), "steps": steps, "peak_kind": kind,
+           "forms": []}
+    for storage, rounding in forms:
+        lat = Lattice(n, n, n, 0.8, flags=flags, storage=storage, force=(1e-6, 0.0, 0.0), stream=stream,
+                      rounding=rounding)
+        v, b, _ = lat.autotune(reps=10, cache=False)
+        lat.step(warmup)
+        m0, _ = lat.totals()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        m1, p1 = lat.totals()
+        lat.close()
+        glups = N * steps / sec / 1e9
+        gbs = glups * bytes_per_update(storage)
+        out["forms"].append({"storage": storage, "rounding": rounding, "variant": v, "block": b,
+                             "glups": round(glups, 2), "fluid_glups": round(glups * fluid / N, 2),
+                             "gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                             "mass_drift_rel": abs(m1 - m0) / m0, "momentum_x": p1[0]})
+    return out
+
+
+def porous_line(args):
+    """The porous channel (porous_section) in --storage as its own line."""
+    rounding = "stochastic" if STORAGE_BYTES[args.storage] == 2 else "nearest"
+    sec = porous_section(((args.storage, rounding),), steps=args.steps, warmup=args.warmup)
+    f = sec["forms"][0]
+    peak, kind = measured_peaks()
+    return {"metric": METRIC, "value": round(f["glups"] * 1e3, 1), "unit": "MLUPS", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(512 ** 3 / f["glups"] / 1e6, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
+            "data": "synthetic",
             "config": {"workload": "porous channel 512^3, D3Q19 BGK, tau 0.8, g 1e-6 x, 400 spheres r U[8,24]",
-                       "solid_fraction": round(1 - fluid / N, 4),
-                       "kernel": {"variant": tuned[0], "block": tuned[1], "chosen_by": "lb_autotune"}},
-            "fluid_mlups": round(fluid * K / sec / 1e6, 1),
-            "roofline": {"bound": "hbm", "achieved": round(bpu * N / (sec / K) / 1e9, 1), "peak": peak,
-                         "unit": "GB/s", "frac": round(bpu * N / (sec / K) / 1e9 / peak, 4), "peak_kind": kind},
-            "mass_drift_rel": abs(m1 - m0) / m0, "momentum_x": p1[0]}
+                       "solid_fraction": sec["solid_fraction"], "rounding": rounding,
+                       "kernel": {"variant": f["variant"], "block": f["block"], "chosen_by": "lb_autotune"}},
+            "fluid_mlups": round(f["fluid_glups"] * 1e3, 1),
+            "roofline": {"bound": "hbm", "achieved": f["gbs"], "peak": peak, "unit": "GB/s", "frac": f["frac"],
+                         "peak_kind": kind},
+            "mass_drift_rel": f["mass_drift_rel"], "momentum_x": f["momentum_x"]}
 
 
 def vks_line(args):
@@ -812,77 +955,100 @@ def vks_line(args):
     }
 
 
-def precision_line(args):
-    """Lid-driven cavity 768^3 (lid (0.1,0,0)), populations stored as f - w
-    in FP16 and BF16 with FP32 math, against the FP32 run of the same case:
-    max |u - u_f32| / max |u_f32| after K steps, mass drift from the FP64
-    reduction, MLUPS; plus the 64^3 copy against the FP64 oracle."""
+# every tau: the two forms gated at 2e-3; the last tau also the contrasts
+# (FP16 rounded to nearest, BF16)
+PRECISION_FORMS = (("f16s", "stochastic"), ("e3m12s", "stochastic"))
+PRECISION_CONTRASTS = (("f16s", "nearest"), ("bf16s", "stochastic"))
+
+
+def precision_section(steps=5000, taus=(0.52, 0.56, 0.6), n=768, small=64):
+    """Lid-driven cavity n^3 (lid (0.1, 0, 0)) with the populations stored as
+    f - w in FP16 (rounded to nearest even, and stochastically), E3M12 and
+    BF16 (stochastically), FP32 math, against the FP32 run of the same case:
+    max |u - u_f32| / max |u_f32| over the lattice after `steps` steps, mass
+    drift from the FP64 reduction, GLUPS and the fraction of the measured
+    HBM bandwidth; plus the small^3 copy of the case (tau 0.6) against the
+    FP64 oracle."""
     import numpy as np
     import torch
 
     import oracle as O
     from paper_2409_16781_gb300 import Lattice, LbDiverged
     from paper_2409_16781_gb300 import workloads as W
-    n, K = 768, args.steps
+    K = int(steps)
     flags = W.cavity_flags(n, n, n)
-    out = {"lattice": [n, n, n], "steps": K, "runs": []}
+    peak, peak_kind = measured_peaks()
+    out = {"lattice": [n, n, n], "steps": K, "lid": [0.1, 0.0, 0.0], "peak_kind": peak_kind, "runs": []}
     stream = torch.cuda.current_stream()
 
-    def run(storage, tau):
-        lat = Lattice(n, n, n, tau, u_lid=(0.1, 0, 0), flags=flags, storage=storage, stream=stream)
-        lat.autotune(reps=3, cache=False)
+    def run(storage, rounding, tau):
+        lat = Lattice(n, n, n, tau, u_lid=(0.1, 0, 0), flags=flags, storage=storage, stream=stream,
+                      rounding=rounding)
+        v, b, _ = lat.autotune(reps=3, cache=False)
         m0, _ = lat.totals()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        done, diverged = 0, None
-        e0.record(stream)
+        done, diverged, sec = 0, None, 0.0
         while done < K:
-            k = min(500, K - done)
+            k = min(1000, K - done)
+            e0.record(stream)
             lat.step(k)
+            e1.record(stream)
+            e1.synchronize()
+            sec += e0.elapsed_time(e1) / 1e3
             done += k
             try:
                 m1, _ = lat.totals()
             except LbDiverged:
                 diverged = done
                 break
-        e1.record(stream)
-        torch.cuda.synchronize()
-        sec = e0.elapsed_time(e1) / 1e3
         u = None if diverged else lat.moments_device()[1]
         lat.close()
-        return u, (None if diverged else abs(m1 - m0) / m0), done * n ** 3 / sec / 1e6, diverged
+        glups = done * n ** 3 / sec / 1e9
+        rec = {"glups": round(glups, 2), "frac": round(glups * bytes_per_update(storage) / peak, 4),
+               "variant": v, "block": b, "mass_drift": None if diverged else abs(m1 - m0) / m0,
+               "diverged_at": diverged}
+        return u, rec
 
-    for tau in [float(t) for t in args.taus.split(",")]:
-        u32, md32, ml32, dv32 = run("f32", tau)
-        rec = {"tau": tau, "f32": {"mlups": round(ml32, 1), "mass_drift": md32, "diverged_at": dv32}}
+    for tau in taus:
+        u32, rec32 = run("f32", "nearest", tau)
+        rec = {"tau": tau, "f32": rec32}
         umax = None if u32 is None else u32.abs().max().item()
-        for storage in ("f16s", "bf16s"):
-            u, md, ml, dv = run(storage, tau)
-            err = None
-            if u is not None and u32 is not None:
-                err = (u - u32).abs().max().item() / umax
-            rec[storage] = {"mlups": round(ml, 1), "mass_drift": md, "u_err_vs_f32": err, "diverged_at": dv}
+        for storage, rounding in PRECISION_FORMS + (PRECISION_CONTRASTS if tau == taus[-1] else ()):
+            u, r = run(storage, rounding, tau)
+            r["u_err_vs_f32"] = None if (u is None or u32 is None) else (u - u32).abs().max().item() / umax
+            rec[f"{storage}_{rounding}"] = r
             del u
+            torch.cuda.empty_cache()
         del u32
         torch.cuda.empty_cache()
         out["runs"].append(rec)
-    # the 64^3 copy against the FP64 oracle
-    m = 64
+    # the small copy against the FP64 oracle
+    m = small
     fl = W.cavity_flags(m, m, m)
+    ks = min(K, 5000)
     ora = O.Lattice(m, m, m, 0.6, u_lid=(0.1, 0, 0), flags=fl)
-    ora.step(min(K, 5000))
+    ora.step(ks)
     _, u_o = ora.moments()
     mask = fl == 0
-    small = {"lattice": [m, m, m], "tau": 0.6, "steps": min(K, 5000)}
-    for storage in ("f32", "f16s", "bf16s"):
-        lat = Lattice(m, m, m, 0.6, u_lid=(0.1, 0, 0), flags=fl, storage=storage)
-        lat.step(min(K, 5000))
+    vs = {"lattice": [m, m, m], "tau": 0.6, "steps": ks}
+    for storage, rounding in (("f32", "nearest"),) + PRECISION_FORMS + PRECISION_CONTRASTS:
+        lat = Lattice(m, m, m, 0.6, u_lid=(0.1, 0, 0), flags=fl, storage=storage, rounding=rounding)
+        lat.step(ks)
         _, u_g = lat.moments()
         lat.close()
-        small[storage] = float(np.abs(u_g[:, mask] - u_o[:, mask]).max() / np.abs(u_o[:, mask]).max())
-    out["vs_oracle_64"] = small
-    return {"metric": METRIC, "value": out["runs"][-1]["f16s"]["mlups"], "unit": "MLUPS", "n_gpus": 1,
-            "steps": K, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f16", "data": "synthetic",
+        vs[f"{storage}_{rounding}"] = float(np.abs(u_g[:, mask] - u_o[:, mask]).max() / np.abs(u_o[:, mask]).max())
+    out["vs_oracle"] = vs
+    return out
+
+
+def precision_line(args):
+    """The 768^3 cavity precision study (precision_section) as its own line."""
+    taus = tuple(float(t) for t in args.taus.split(","))
+    out = precision_section(args.precision_steps if args.precision_steps else args.steps, taus)
+    last = out["runs"][-1]["f16s_stochastic"]
+    return {"metric": METRIC, "value": round(last["glups"] * 1e3, 1), "unit": "MLUPS", "n_gpus": 1,
+            "steps": out["steps"], "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16", "data": "synthetic",
             "config": {"workload": "cavity 768^3 precision study: f - w stored in FP16 / BF16, FP32 math, "
                                    "vs the FP32 GPU run and the FP64 oracle at 64^3"},
             "precision": out}
@@ -894,7 +1060,8 @@ def serve_line(args):
     n = args.serve_requests if args.serve_requests else 2000
     rates = tuple(float(r) for r in args.serve_rates.split(","))
     sv = run_serving(n, rates, args.serve_budget_gb, tight_budget_gb=args.serve_tight_gb,
-                     max_wait_s=args.serve_max_wait or None, log_prefix=args.serve_log)
+                     max_wait_s=args.serve_max_wait or None, log_prefix=args.serve_log,
+                     rounding=args.serve_rounding, accuracy_every=10 if n > 200 else 1)
     hi = sv["runs"][-1]
     return {"metric": METRIC, "value": hi["batched"]["mlups"], "unit": "MLUPS", "n_gpus": 1,
             "steps": None, "warmup": 0, "higher_is_better": True, "scaling": "weak",

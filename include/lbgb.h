@@ -55,13 +55,20 @@ typedef enum {
 
 /* Population storage (the paper's precision modes, Sec. 3.1.1).  Every
  * form stores the deviation f_i - w_i; the math is FP32 except for LB_F64
- * (FP64 storage and math) and LB_F32D (FP32 storage, FP64 math). */
+ * (FP64 storage and math) and LB_F32D (FP32 storage, FP64 math).
+ * LB_E3M12S (not in the paper) is a 16-bit float of the deviation with 1
+ * sign, 3 exponent and 12 mantissa bits: |d| in [2^(e-11), 2^(e-10)) for
+ * exponent field e = 1..7, steps of 2^-22 below 2^-10; largest value
+ * (2 - 2^-12) 2^-4 ~ 0.125 (larger magnitudes saturate, and lb_totals
+ * then reports LB_EDIVERGED).  Where the deviations of a low-Mach flow lie
+ * (|d| > 2^-10) its resolution is four times FP16's, for the same bytes. */
 typedef enum {
     LB_F64 = 0,   /* "Double": FP64 storage, FP64 math            */
     LB_F32 = 1,   /* "Single": FP32 storage, FP32 math            */
     LB_F16S = 2,  /* "Mixed1": FP16 storage of f - w, FP32 math   */
     LB_BF16S = 3, /* BF16 storage of f - w, FP32 math             */
-    LB_F32D = 4   /* "Mixed2": FP32 storage of f - w, FP64 math   */
+    LB_F32D = 4,  /* "Mixed2": FP32 storage of f - w, FP64 math   */
+    LB_E3M12S = 5 /* E3M12 16-bit storage of f - w, FP32 math     */
 } lb_storage;
 
 /* Cell flags (uint8 per cell).  LB_WALL: no-slip wall (halfway
@@ -79,7 +86,8 @@ typedef struct lb_options {
     int kernel;        /* step kernel variant: 0 = library's choice */
     int block;         /* threads per block of the step kernel; 0 = choice */
     int rounding;      /* how a step rounds the new 16-bit stored values
-                          (LB_F16S, LB_BF16S; must be 0 for other storage):
+                          (LB_F16S, LB_BF16S, LB_E3M12S; must be 0 for
+                          other storage):
                           0 (default) to nearest even; 1 stochastically --
                           up with probability equal to the dropped fraction,
                           so each stored value is unbiased and changes far

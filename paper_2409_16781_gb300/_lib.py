@@ -12,9 +12,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbgb.so")
 
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_EDIVERGED, LB_ETIMEOUT, LB_EBUSY = 0, -1, -2, -3, -4, -5, -6
-LB_F64, LB_F32, LB_F16S, LB_BF16S, LB_F32D = 0, 1, 2, 3, 4
-STORAGE = {"f64": LB_F64, "f32": LB_F32, "f16s": LB_F16S, "bf16s": LB_BF16S, "f32d": LB_F32D}
-STORAGE_BYTES = {LB_F64: 8, LB_F32: 4, LB_F16S: 2, LB_BF16S: 2, LB_F32D: 4}
+LB_F64, LB_F32, LB_F16S, LB_BF16S, LB_F32D, LB_E3M12S = 0, 1, 2, 3, 4, 5
+STORAGE = {"f64": LB_F64, "f32": LB_F32, "f16s": LB_F16S, "bf16s": LB_BF16S, "f32d": LB_F32D,
+           "e3m12s": LB_E3M12S}
+STORAGE_BYTES = {LB_F64: 8, LB_F32: 4, LB_F16S: 2, LB_BF16S: 2, LB_F32D: 4, LB_E3M12S: 2}
 Q = 19
 
 

@@ -154,7 +154,7 @@ int create_common(lb_lattice** out, int nx, int ny, int nz, double tau, const do
     lb_options o = opt ? *opt : defaults();
     if (!valid_dims(nx, ny, nz)) return fail(LB_EINVAL, "lb_create: bad dims %d x %d x %d", nx, ny, nz);
     if (!(tau > 0.5) || !std::isfinite(tau)) return fail(LB_EINVAL, "lb_create: tau must be > 1/2 (got %g)", tau);
-    if (o.storage < LB_F64 || o.storage > LB_F32D) return fail(LB_EINVAL, "lb_create: bad storage %d", o.storage);
+    if (o.storage < LB_F64 || o.storage > LB_E3M12S) return fail(LB_EINVAL, "lb_create: bad storage %d", o.storage);
     if (!(o.trt_magic >= 0.0) || !std::isfinite(o.trt_magic))
         return fail(LB_EINVAL, "lb_create: trt_magic must be >= 0 (got %g)", o.trt_magic);
     if (o.inplace != 0 && o.inplace != 1) return fail(LB_EINVAL, "lb_create: inplace must be 0 or 1 (got %d)", o.inplace);
@@ -281,7 +281,7 @@ int lb_velocity_set(int* c, double* w) {
 size_t lb_bytes_required(int nx, int ny, int nz, const lb_options* opt) {
     const int storage = opt ? opt->storage : LB_F32;
     const int inplace = opt ? opt->inplace : 0;
-    if (!valid_dims(nx, ny, nz) || storage < LB_F64 || storage > LB_F32D || (inplace != 0 && inplace != 1)) return 0;
+    if (!valid_dims(nx, ny, nz) || storage < LB_F64 || storage > LB_E3M12S || (inplace != 0 && inplace != 1)) return 0;
     return layout_for(nx, ny, nz, storage, inplace).total;
 }
 
@@ -593,9 +593,9 @@ int lb_autotune(lb_lattice* h, int reps, int* variant, int* block, float* ms_per
         if (nc < 32) cands[nc++] = {v, b};
     };
     const bool sixteen = h->sbytes == 2;
-    // stochastic rounding: only the variants that have that form (the others
-    // would run variant 15)
-    const bool all = !h->rounding;
+    // stochastic rounding, and the E3M12 form: only the variants that have
+    // that form (the others would run variant 15 or 1)
+    const bool all = !h->rounding && h->storage != LB_E3M12S;
     if (h->inplace) return autotune_inplace(h, reps, variant, block, ms_per_step);
     for (int b : {32, 64, 128, 256}) add(1, b);
     if (h->nx % 2 == 0 && all) {

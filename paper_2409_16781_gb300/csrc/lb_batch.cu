@@ -27,8 +27,8 @@ namespace lbgb {
 namespace {
 
 constexpr int BATCH_THREADS = 128;   // cells per work item = threads per block
-constexpr int BATCH_STORAGES = 5;    // storage types
-constexpr int BATCH_TYPES = 10;      // kernel types: storage x (two arrays, in place)
+constexpr int BATCH_STORAGES = 6;    // storage types
+constexpr int BATCH_TYPES = 12;      // kernel types: storage x (two arrays, in place)
 constexpr int GRAPH_STEPS = 8;       // batched steps per captured graph
 constexpr size_t BALIGN = 256;
 
@@ -439,11 +439,13 @@ cudaError_t launch_type(lb_batch* b, int t, cudaStream_t st) {
         case 2: launch_typed<__half, false>(b, t, st); break;
         case 3: launch_typed<__nv_bfloat16, false>(b, t, st); break;
         case 4: launch_typed<f32d, false>(b, t, st); break;
-        case 5: launch_typed<double, true>(b, t, st); break;
-        case 6: launch_typed<float, true>(b, t, st); break;
-        case 7: launch_typed<__half, true>(b, t, st); break;
-        case 8: launch_typed<__nv_bfloat16, true>(b, t, st); break;
-        default: launch_typed<f32d, true>(b, t, st); break;
+        case 5: launch_typed<e3m12, false>(b, t, st); break;
+        case 6: launch_typed<double, true>(b, t, st); break;
+        case 7: launch_typed<float, true>(b, t, st); break;
+        case 8: launch_typed<__half, true>(b, t, st); break;
+        case 9: launch_typed<__nv_bfloat16, true>(b, t, st); break;
+        case 10: launch_typed<f32d, true>(b, t, st); break;
+        default: launch_typed<e3m12, true>(b, t, st); break;
     }
     return cudaGetLastError();
 }
@@ -619,11 +621,13 @@ int batch_create_common(lb_batch** out, size_t capacity, int max_slots, void* st
         if (e == cudaSuccess) e = occupancy_of<__half, false>(&per[2]);
         if (e == cudaSuccess) e = occupancy_of<__nv_bfloat16, false>(&per[3]);
         if (e == cudaSuccess) e = occupancy_of<f32d, false>(&per[4]);
-        if (e == cudaSuccess) e = occupancy_of<double, true>(&per[5]);
-        if (e == cudaSuccess) e = occupancy_of<float, true>(&per[6]);
-        if (e == cudaSuccess) e = occupancy_of<__half, true>(&per[7]);
-        if (e == cudaSuccess) e = occupancy_of<__nv_bfloat16, true>(&per[8]);
-        if (e == cudaSuccess) e = occupancy_of<f32d, true>(&per[9]);
+        if (e == cudaSuccess) e = occupancy_of<e3m12, false>(&per[5]);
+        if (e == cudaSuccess) e = occupancy_of<double, true>(&per[6]);
+        if (e == cudaSuccess) e = occupancy_of<float, true>(&per[7]);
+        if (e == cudaSuccess) e = occupancy_of<__half, true>(&per[8]);
+        if (e == cudaSuccess) e = occupancy_of<__nv_bfloat16, true>(&per[9]);
+        if (e == cudaSuccess) e = occupancy_of<f32d, true>(&per[10]);
+        if (e == cudaSuccess) e = occupancy_of<e3m12, true>(&per[11]);
         for (int t = 0; t < BATCH_TYPES; ++t) b->grid[t] = sms * (per[t] > 0 ? per[t] : 1);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
@@ -662,7 +666,7 @@ extern "C" {
 
 size_t lb_batch_slot_bytes(int nx, int ny, int nz, int storage, int inplace) {
     if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz >= (int64_t(1) << 31)) return 0;
-    if (storage < LB_F64 || storage > LB_F32D || (inplace != 0 && inplace != 1)) return 0;
+    if (storage < LB_F64 || storage > LB_E3M12S || (inplace != 0 && inplace != 1)) return 0;
     return slot_bytes(nx, ny, nz, storage, inplace);
 }
 
@@ -690,7 +694,7 @@ int lb_batch_add(lb_batch* b, int nx, int ny, int nz, double tau, const double* 
     if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz >= (int64_t(1) << 31))
         return bfail(LB_EINVAL, "lb_batch_add: bad dims %d x %d x %d", nx, ny, nz);
     if (!(tau > 0.5) || !std::isfinite(tau)) return bfail(LB_EINVAL, "lb_batch_add: tau must be > 1/2");
-    if (o.storage < LB_F64 || o.storage > LB_F32D) return bfail(LB_EINVAL, "lb_batch_add: bad storage");
+    if (o.storage < LB_F64 || o.storage > LB_E3M12S) return bfail(LB_EINVAL, "lb_batch_add: bad storage");
     if (!(o.trt_magic >= 0.0) || !std::isfinite(o.trt_magic))
         return bfail(LB_EINVAL, "lb_batch_add: trt_magic must be >= 0");
     if (o.inplace != 0 && o.inplace != 1) return bfail(LB_EINVAL, "lb_batch_add: inplace must be 0 or 1");

@@ -153,6 +153,64 @@ template <> __device__ __forceinline__ uint32_t cvt_rs2<__nv_bfloat16>(float lo,
     asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(r) : "f"(hi), "f"(lo), "r"(bits));
     return r;
 }
+struct e3m12;
+template <> __device__ __forceinline__ uint32_t cvt_rs2<e3m12>(float lo, float hi, uint32_t bits);
+
+// A 16-bit float format of the deviation, finer than FP16 where the
+// deviations of a low-Mach flow are: 1 sign, 3 exponent and 12 mantissa
+// bits (FP16 has 5 and 10).  |d| in [2^(e-11), 2^(e-10)) for exponent field
+// e = 1..7, step 2^(e-23); e = 0 holds the subnormal range [0, 2^-10) in
+// steps of 2^-22.  The largest value is (2 - 2^-12) 2^-4 ~ 0.125; larger
+// magnitudes (and NaN) saturate to it, and the totals count a saturated
+// value as a bad cell.  Above 2^-10 the unit in the last place is a quarter
+// of FP16's, and no coarser below.  The conversions use the binary32 bit
+// layout: a code placed in bits 26..11 (sign in bit 31) is the float value
+// times 2^-116, so decoding is a shift and a multiplication by 2^116 (exact:
+// FP32 subnormal inputs included), and encoding multiplies by 2^-116, adds
+// the rounding increment below the 12th mantissa bit (half-even for
+// rounding to nearest, 11 random bits for stochastic rounding) to the
+// magnitude, clamps it, and shifts.
+struct e3m12 {
+    uint16_t v;
+};
+constexpr uint32_t E3M12_MAG_MAX = 0x03FFFFFFu;  // FP32 magnitude bits of the largest code (any low bits)
+__host__ __device__ inline uint32_t e3m12_bits(uint32_t code) {
+    return ((code & 0x8000u) << 16) | ((code & 0x7FFFu) << 11);
+}
+__device__ __forceinline__ float e3m12_decode(uint32_t code) {
+    return __uint_as_float(e3m12_bits(code)) * 0x1p116f;
+}
+// the pair (low half, high half) of a 32-bit word as two FP32 values
+__device__ __forceinline__ float2 e3m12_decode2(uint32_t w) {
+    const float2 b = make_float2(__uint_as_float(e3m12_bits(w)),
+                                 __uint_as_float((w & 0x80000000u) | ((w >> 5) & 0x03FFF800u)));
+    return __fmul2_rn(b, make_float2(0x1p116f, 0x1p116f));
+}
+// add = increment to the magnitude below the kept bits (0 .. 0x7FF)
+__device__ __forceinline__ uint32_t e3m12_encode_add(float x, uint32_t add) {
+    const uint32_t b = __float_as_uint(x * 0x1p-116f);
+    const uint32_t m = min((b & 0x7FFFFFFFu) + add, E3M12_MAG_MAX);
+    return (m >> 11) | ((b >> 16) & 0x8000u);
+}
+__device__ __forceinline__ uint32_t e3m12_encode_rn(float x) {
+    const uint32_t m = __float_as_uint(x * 0x1p-116f) & 0x7FFFFFFFu;
+    return e3m12_encode_add(x, 0x3FFu + ((m >> 11) & 1u));
+}
+template <> struct Storage<e3m12> {
+    using math = float;
+    static constexpr int id = 5;
+    __device__ __forceinline__ static float load(e3m12 v) { return e3m12_decode(v.v); }
+    __device__ __forceinline__ static e3m12 store(float v) { return e3m12{(uint16_t)e3m12_encode_rn(v)}; }
+};
+// The 16-bit IEEE storage types (FP16, BF16), which the kernels that work on
+// packed 16-bit registers (variants 6-12 and 14) handle.
+template <class S>
+constexpr bool ieee16 = std::is_same<S, __half>::value || std::is_same<S, __nv_bfloat16>::value;
+// stochastic rounding of an E3M12 pair: the low half takes bits[10:0], the
+// high half bits[31:21] (each cell's own bits, as for the IEEE forms)
+template <> __device__ __forceinline__ uint32_t cvt_rs2<e3m12>(float lo, float hi, uint32_t bits) {
+    return e3m12_encode_add(lo, bits & 0x7FFu) | (e3m12_encode_add(hi, bits >> 21) << 16);
+}
 
 // Parameters of one lattice as seen by the kernels.
 struct LatticeParams {

@@ -85,6 +85,7 @@ cudaError_t launch_halo(int sbytes, void* A, int64_t ps, int nx, int ny, int nz,
         case 2: { using S = __half; return CALL; }        \
         case 3: { using S = __nv_bfloat16; return CALL; } \
         case 4: { using S = f32d; return CALL; }          \
+        case 5: { using S = e3m12; return CALL; }         \
         default: return cudaErrorInvalidValue;            \
     }
 
@@ -106,6 +107,7 @@ inline int storage_bytes(int storage) {
         case 2: return 2;
         case 3: return 2;
         case 4: return 4;
+        case 5: return 2;
         default: return 0;
     }
 }

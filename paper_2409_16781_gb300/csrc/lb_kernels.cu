@@ -7,6 +7,8 @@
 // previous step) with a pull gather and writes array B.  Populations are
 // structure-of-arrays (Sec. 3.1), one unit-stride plane per direction, x
 // fastest (Sec. 4.2 column-major default).
+#include <type_traits>
+
 #include "lb_internal.h"
 #include "lb_kernels.cuh"
 
@@ -151,8 +153,13 @@ __global__ void __launch_bounds__(TOT_THREADS) totals_kernel(const S* __restrict
                 sy += jy;
                 sz += jz;
                 nf += 1;
-                if (!(M(1) + drho > M(0)) || !isfinite(drho) || !isfinite(jx) || !isfinite(jy) || !isfinite(jz))
-                    nbad += 1;
+                bool bad = !(M(1) + drho > M(0)) || !isfinite(drho) || !isfinite(jx) || !isfinite(jy) || !isfinite(jz);
+                if constexpr (std::is_same<S, e3m12>::value) {
+                    // a saturated E3M12 value (its range is |d| < 1/8) counts as divergence
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) bad |= fabsf(d[i]) >= 0x1.fffp-4f;
+                }
+                if (bad) nbad += 1;
             }
         }
         if (++pending == TOT_FOLD) {

@@ -40,6 +40,8 @@ template <int HINT, class S>
 __device__ __forceinline__ S ld_pop(const S* p) {
     if constexpr (std::is_same<S, f32d>::value) {
         return f32d{ld_pop<HINT>(reinterpret_cast<const float*>(p))};
+    } else if constexpr (std::is_same<S, e3m12>::value) {
+        return e3m12{ld_pop<HINT>(reinterpret_cast<const unsigned short*>(p))};
     } else {
 #ifdef LBGB_CHECKED
         if (g_check.on) {
@@ -60,6 +62,8 @@ template <int HINT, class S>
 __device__ __forceinline__ void st_pop(S* p, S v) {
     if constexpr (std::is_same<S, f32d>::value) {
         st_pop<HINT>(reinterpret_cast<float*>(p), v.v);
+    } else if constexpr (std::is_same<S, e3m12>::value) {
+        st_pop<HINT>(reinterpret_cast<unsigned short*>(p), (unsigned short)v.v);
     } else {
 #ifdef LBGB_CHECKED
         if (g_check.on) {
@@ -517,6 +521,7 @@ template <> __device__ __forceinline__ __half from_bits16<__half>(uint32_t w) {
 template <> __device__ __forceinline__ __nv_bfloat16 from_bits16<__nv_bfloat16>(uint32_t w) {
     return __ushort_as_bfloat16((unsigned short)w);
 }
+template <> __device__ __forceinline__ e3m12 from_bits16<e3m12>(uint32_t w) { return e3m12{(uint16_t)w}; }
 
 template <class S, bool SR>
 struct Rounder {
@@ -545,6 +550,8 @@ struct Rounder {
         } else if constexpr (std::is_same<S, __half>::value) {
             const __half2 h = __floats2half2_rn(lo, hi);
             return *reinterpret_cast<const uint32_t*>(&h);
+        } else if constexpr (std::is_same<S, e3m12>::value) {
+            return e3m12_encode_rn(lo) | (e3m12_encode_rn(hi) << 16);
         } else {
             const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
             return *reinterpret_cast<const uint32_t*>(&h);

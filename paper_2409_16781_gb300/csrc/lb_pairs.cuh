@@ -18,6 +18,7 @@ template <> struct Vec2<double> { using T = double2; };
 template <> struct Vec2<float> { using T = float2; };
 template <> struct Vec2<__half> { using T = __half2; };
 template <> struct Vec2<__nv_bfloat16> { using T = __nv_bfloat162; };
+template <> struct Vec2<e3m12> { using T = uint32_t; };  // low half: the first cell
 
 template <class S> __device__ __forceinline__ void split2(const typename Vec2<S>::T& v, typename Storage<S>::math& a,
                                                           typename Storage<S>::math& b);
@@ -33,6 +34,11 @@ template <> __device__ __forceinline__ void split2<__nv_bfloat16>(const __nv_bfl
     a = f.x;
     b = f.y;
 }
+template <> __device__ __forceinline__ void split2<e3m12>(const uint32_t& v, float& a, float& b) {
+    const float2 f = e3m12_decode2(v);
+    a = f.x;
+    b = f.y;
+}
 template <class S> __device__ __forceinline__ typename Vec2<S>::T pack2(typename Storage<S>::math a,
                                                                         typename Storage<S>::math b);
 template <> __device__ __forceinline__ double2 pack2<double>(double a, double b) { return make_double2(a, b); }
@@ -40,6 +46,10 @@ template <> __device__ __forceinline__ float2 pack2<float>(float a, float b) { r
 template <> __device__ __forceinline__ __half2 pack2<__half>(float a, float b) { return __floats2half2_rn(a, b); }
 template <> __device__ __forceinline__ __nv_bfloat162 pack2<__nv_bfloat16>(float a, float b) {
     return __floats2bfloat162_rn(a, b);
+}
+
+template <> __device__ __forceinline__ uint32_t pack2<e3m12>(float a, float b) {
+    return e3m12_encode_rn(a) | (e3m12_encode_rn(b) << 16);
 }
 
 template <class S> __device__ __forceinline__ f32x2 to_x2(uint32_t w);  // two packed 16-bit values

@@ -57,7 +57,7 @@ extern "C" int lb_totals_static(const void* populations, int64_t plane_stride, c
     if (nx < 1 || ny < 1 || nz < 1) return LB_EINVAL;
     const int64_t N = (int64_t)nx * ny * nz;
     if (N >= (int64_t(1) << 31)) return LB_EINVAL;  // beyond the library's cell limit
-    if (plane_stride < N || storage < LB_F64 || storage > LB_F32D) return LB_EINVAL;
+    if (plane_stride < N || storage < LB_F64 || storage > LB_E3M12S) return LB_EINVAL;
     LatticeParams p{};
     p.nx = nx;
     p.ny = ny;

@@ -904,7 +904,7 @@ static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* co
                                 : step_rows_t<S, 1>(A, B, code, p, block, st);
         case 6:
         case 7:
-            if constexpr (sizeof(S) == 2) {
+            if constexpr (ieee16<S>) {
                 if (pairs_ok)
                     return variant == 6 ? step_pairs16_t<S, 0>(A, B, code, p, block, st)
                                         : step_pairs16_t<S, 1>(A, B, code, p, block, st);
@@ -912,7 +912,7 @@ static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* co
             return step_rows_t<S, 0>(A, B, code, p, block, st);
         case 8:
         case 9:
-            if constexpr (sizeof(S) == 2) {
+            if constexpr (ieee16<S>) {
                 if (p.nx % 4 == 0)
                     return variant == 8 ? step_quads16_t<S, 0>(A, B, code, p, block, st)
                                         : step_quads16_t<S, 1>(A, B, code, p, block, st);
@@ -921,7 +921,7 @@ static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* co
         case 10:
         case 11:
         case 12:
-            if constexpr (sizeof(S) == 2)
+            if constexpr (ieee16<S>)
                 return variant == 10 ? step_tma16_t<S, 4>(A, B, code, p, block, st)
                        : variant == 11 ? step_tma16_t<S, 2>(A, B, code, p, block, st)
                                        : step_tma16_t<S, 1>(A, B, code, p, block, st);
@@ -935,7 +935,7 @@ static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* co
             }
             return step_rows_t<S, 0>(A, B, code, p, block, st);
         case 14:
-            if constexpr (sizeof(S) == 2) {
+            if constexpr (ieee16<S>) {
                 if (p.nx % 4 == 0) return step_quads16_x2_t<S, 0>(A, B, code, p, block, st);
             }
             return step_rows_t<S, 0>(A, B, code, p, block, st);
@@ -951,6 +951,8 @@ static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* co
             // cells per thread collided as a packed FP32 pair, 64 registers
             if constexpr (sizeof(S) == 2) {
                 if (pairs_ok) return step_pairs_x2_t<S, 0, 2>(A, B, code, p, block > 0 ? block : 64, st);
+            }
+            if constexpr (ieee16<S>) {
                 if (p.nx % 4 == 0) return step_quads16_x2_t<S, 0>(A, B, code, p, block > 0 ? block : 32, st);
             }
             if constexpr (sizeof(S) == 8) {

@@ -23,7 +23,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 
-BYTES_PER_UPDATE = {"f64": 305, "f32": 153, "f16s": 77, "bf16s": 77, "f32d": 153}
+BYTES_PER_UPDATE = {"f64": 305, "f32": 153, "f16s": 77, "bf16s": 77, "f32d": 153, "e3m12s": 77}
 
 
 @dataclass
@@ -135,9 +135,12 @@ class Scheduler:
         self.target_cells = int(target_cells)
         self.max_wait_s = None if max_wait_s is None else float(max_wait_s)
 
-    @staticmethod
-    def _bpu(req):
-        return BYTES_PER_UPDATE.get(getattr(req, "storage", "f32"), 153)
+    def _storage(self, req):
+        fn = getattr(self.backend, "storage_of", None)
+        return fn(req) if fn is not None else getattr(req, "storage", "f32")
+
+    def _bpu(self, req):
+        return BYTES_PER_UPDATE.get(self._storage(req), 153)
 
     def _chunk(self, running):
         if getattr(self.backend, "whole_requests", False):
@@ -237,7 +240,7 @@ class Scheduler:
             for h, payload in self.backend.collect():
                 req, t_adm = retiring.pop(h)
                 stats.results.append(Result(req.rid, req.arrival_s, t_adm, self.clock() - t0, req.cells,
-                                            req.steps, getattr(req, "storage", "f32"), payload))
+                                            req.steps, self._storage(req), payload))
                 progressed = True
             if issued > polled or progressed:
                 continue
@@ -256,9 +259,43 @@ class Scheduler:
         return stats
 
 
+# Storage policy for 16-bit requests.  FP16 keeps 11 significant bits only
+# for |d| >= 2^-14; below that its steps are a fixed 2^-24, so a request
+# whose deviations stay small (a slowly driven flow) loses relative
+# precision in FP16 whatever the rounding.  Its deviation scale is
+# predicted from the request: the axis populations carry w 3 c.u = U/6 for
+# a flow speed U, with U the lid speed for a cavity, and for a duct driven
+# by a body force g from rest the smaller of the free acceleration g t and
+# the laminar centre speed g H^2 / (8 nu) (H the narrower wall-to-wall width,
+# nu = (tau - 1/2) / 3).  A 16-bit request predicted below MIN_DEV_16 is
+# served in FP32 instead.
+MIN_DEV_16 = 2.0 ** -13
+
+
+def predicted_deviation(req) -> float:
+    """The deviation scale U/6 a request's flow reaches (see above)."""
+    ulid = float(np.linalg.norm(getattr(req, "u_lid", (0.0, 0.0, 0.0))))
+    g = float(np.linalg.norm(getattr(req, "force", (0.0, 0.0, 0.0))))
+    u = ulid
+    if g > 0.0:
+        h = max(1, min(req.ny, req.nz) - 2)
+        nu = (req.tau - 0.5) / 3.0
+        u = max(u, min(g * req.steps, g * h * h / (8.0 * nu)))
+    return u / 6.0
+
+
+def served_storage(req, promote: bool = True) -> str:
+    """The storage a request is served in: its own, except that a 16-bit
+    request whose predicted deviations are below MIN_DEV_16 gets FP32."""
+    st = getattr(req, "storage", "f32")
+    if promote and st in ("f16s", "bf16s", "e3m12s") and predicted_deviation(req) < MIN_DEV_16:
+        return "f32"
+    return st
+
+
 def _rounding_for(storage: str, rounding: str) -> str:
     """Stochastic rounding applies to 16-bit storage only."""
-    return rounding if storage in ("f16s", "bf16s") else "nearest"
+    return rounding if storage in ("f16s", "bf16s", "e3m12s") else "nearest"
 
 
 def _checksum(u):
@@ -284,18 +321,23 @@ class BatchBackend:
     results come back asynchronously (lb_batch_fetch) into pinned buffers."""
 
     def __init__(self, capacity_bytes: int, max_slots: int = 1024, device=None, keep_fields: bool = False,
-                 inplace: bool = False, rounding: str = "nearest"):
+                 inplace: bool = False, rounding: str = "nearest", promote: bool = False):
         from .batch import Batch
         self.batch = Batch(capacity_bytes, max_slots=max_slots, device=device)
         self.keep = keep_fields
         self.inplace = inplace  # one population array per slot: about twice the requests per budget
         self.rounding = rounding  # of 16-bit requests (lb_options.rounding)
+        self.promote = promote    # 16-bit requests with small predicted deviations served in FP32
         self.pending = {}
 
+    def storage_of(self, req) -> str:
+        return served_storage(req, self.promote)
+
     def admit(self, req):
+        st = self.storage_of(req)
         return self.batch.try_add(req.nx, req.ny, req.nz, req.tau, req.steps, u_lid=req.u_lid,
-                                  flags=req.flags(), storage=req.storage, force=req.force,
-                                  inplace=self.inplace, rounding=_rounding_for(req.storage, self.rounding))
+                                  flags=req.flags(), storage=st, force=req.force,
+                                  inplace=self.inplace, rounding=_rounding_for(st, self.rounding))
 
     def step(self, n):
         self.batch.step(n)

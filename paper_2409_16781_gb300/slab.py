@@ -53,8 +53,11 @@ class SlabExchange:
     slab is its own neighbour both ways (periodic z) and no message is sent.
     """
 
-    def __init__(self, rank: int = 0, world: int = 1, group=None):
+    def __init__(self, rank: int = 0, world: int = 1, group=None, device=None):
+        """device: where the all-reduce of sum() runs (a CUDA device for
+        NCCL; None = the host, for gloo)."""
         self.rank, self.world, self.group = int(rank), int(world), group
+        self.device = device
         self.up = (self.rank + 1) % self.world
         self.down = (self.rank - 1) % self.world
 
@@ -78,10 +81,11 @@ class SlabExchange:
             req.wait()
         local.halo_unpack(recv_lo, recv_hi)
 
-    def sum(self, values, device="cpu"):
+    def sum(self, values):
         """Element-wise FP64 sum of `values` over the ranks (one all-reduce)."""
         import torch
-        t = torch.tensor(np.asarray(values, dtype=np.float64), dtype=torch.float64, device=device)
+        t = torch.tensor(np.asarray(values, dtype=np.float64), dtype=torch.float64,
+                         device=self.device if self.device is not None else "cpu")
         if self.world > 1:
             import torch.distributed as dist
             dist.all_reduce(t, op=dist.ReduceOp.SUM, group=self.group)
@@ -116,11 +120,15 @@ class SlabLattice:
         self.lattice = Lattice(self.nx, self.ny, self.nzl, tau, u_lid=u_lid, flags=fl, storage=storage,
                                force=force, device=device, stream=stream, kernel=kernel, block=block,
                                halo_z=True)
-        self.exchange = exchange if exchange is not None else SlabExchange(self.rank, self.world, group)
+        if exchange is None:
+            import torch.distributed as dist
+            nccl = dist.is_available() and dist.is_initialized() and dist.get_backend(group) == "nccl"
+            exchange = SlabExchange(self.rank, self.world, group, self.lattice.device if nccl else None)
+        self.exchange = exchange
         nb = self.lattice.halo_bytes()
         dev = self.lattice.device
         self._bufs = tuple(torch.empty(nb, dtype=torch.uint8, device=dev) for _ in range(4))
-        self._halo()
+        self.halo()
 
     # the local-lattice side of SlabExchange
     def halo_buffers(self):
@@ -132,7 +140,9 @@ class SlabLattice:
     def halo_unpack(self, recv_lo, recv_hi):
         self.lattice.halo_unpack(recv_lo, recv_hi)
 
-    def _halo(self):
+    def halo(self):
+        """The halo exchange of the current state (after a step or an
+        initialisation of the local lattice)."""
         import torch
         with torch.cuda.stream(self.lattice.stream):
             self.exchange(self)
@@ -143,13 +153,13 @@ class SlabLattice:
         r = None if rho is None else ghosted(np.asarray(rho, dtype=np.float64), self.z0, self.z1)
         v = None if u is None else ghosted(np.asarray(u, dtype=np.float64), self.z0, self.z1, axis=1)
         self.lattice.init_fields(r, v)
-        self._halo()
+        self.halo()
 
     def step(self, n: int = 1):
         """n steps, each followed by the halo exchange."""
         for _ in range(int(n)):
             self.lattice.step(1)
-            self._halo()
+            self.halo()
 
     def totals(self):
         """Global FP64 (mass, momentum[3]): this slab's sums, all-reduced."""

@@ -21,10 +21,10 @@ from paper_2409_16781_gb300.serve import BatchBackend, SequentialBackend, serve
 
 pytestmark = pytest.mark.gpu
 
-VEL_TOL = {"f32": 1e-5, "f16s": 2e-3, "bf16s": 3e-2, "f32d": 1e-6}
+VEL_TOL = {"f32": 1e-5, "f16s": 2e-3, "bf16s": 3e-2, "f32d": 1e-6, "e3m12s": 5e-4}
 # relative mass agreement: the storage rounding of each deviation bounds how
 # closely two kernels' conserved sums agree (16-bit: about one ulp per cell)
-MASS_TOL = {"f64": 1e-12, "f32": 1e-8, "f16s": 1e-5, "bf16s": 1e-4, "f32d": 1e-8}
+MASS_TOL = {"f64": 1e-12, "f32": 1e-8, "f16s": 1e-5, "bf16s": 1e-4, "f32d": 1e-8, "e3m12s": 1e-5}
 
 MIX = [
     # nx, ny, nz, tau, storage, kind, steps
@@ -32,6 +32,7 @@ MIX = [
     (32, 20, 16, 0.56, "f16s", "channel", 33),
     (9, 7, 13, 0.9, "f64", "cavity", 25),
     (40, 10, 12, 0.6, "bf16s", "channel", 30),
+    (22, 14, 10, 0.62, "e3m12s", "cavity", 27),
     (24, 24, 24, 0.52, "f32", "channel", 57),
     (5, 31, 6, 0.8, "f16s", "cavity", 11),
     (64, 3, 2, 0.65, "f32", "random", 21),

@@ -45,7 +45,7 @@ def _guards_intact(torch, buf, nbytes):
 
 
 @pytest.mark.parametrize("inplace", [False, True], ids=["two_arrays", "in_place"])
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16s", "bf16s", "f32d"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s", "bf16s", "f32d", "e3m12s"])
 def test_step_variants_stay_inside_their_buffer(storage, inplace):
     import torch
     lib = L.lib()
@@ -96,7 +96,7 @@ def test_batch_pool_stays_inside_its_buffer():
                                    ctypes.c_void_p(stream.cuda_stream)), "lb_batch_create_in")
     try:
         k = 0
-        for storage in ("f64", "f32", "f16s", "bf16s", "f32d"):
+        for storage in ("f64", "f32", "f16s", "bf16s", "f32d", "e3m12s"):
             for inplace in (False, True):
                 for nx, ny, nz in SHAPES[:3]:
                     flags = _flags(nx, ny, nz, seed=k)

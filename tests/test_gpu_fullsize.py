@@ -208,6 +208,79 @@ def test_cavity_768_precision(storage, perm):
     lat.close()
 
 
+# The configured precision study: cavity 768^3, lid (0.1, 0, 0), 5000 steps.
+# FP16 storage with stochastic rounding meets 2e-3 of u_max against the FP32
+# run at tau 0.56 and 0.6 (measured 1.8e-3 and 1.2e-3); at tau 0.52 (Re about
+# 1.1e4) it does not: measured 3.9e-3 (rounding to nearest: 2.8e-3), which
+# the bound below records.  The FP32 case is not chaotic there: a 1e-5
+# relative change of the lid speed moves u by 2e-5 of u_max after the same
+# 5000 steps, so the gap is the 16-bit storage's, not the flow's.
+# The E3M12 form (a quarter of FP16's unit in the last place where these
+# deviations lie), rounded stochastically, is held to 2e-3 at every tau.
+BOUND_768 = {0.52: 5e-3, 0.56: 2e-3, 0.6: 2e-3}
+
+
+@pytest.mark.parametrize("tau", sorted(BOUND_768))
+def test_cavity_768_precision_5000_steps(tau):
+    n, K, ulid = 768, 5000, (0.1, 0.0, 0.0)
+    flags = W.cavity_flags(n, n, n)
+    ref = Lattice(n, n, n, tau, u_lid=ulid, flags=flags, storage="f32")
+    ref.step(K)
+    _, u_ref = ref.moments_device()
+    ref.close()
+    umax = u_ref.abs().max().item()
+    for storage, bound in (("f16s", BOUND_768[tau]), ("e3m12s", 2e-3)):
+        lat = Lattice(n, n, n, tau, u_lid=ulid, flags=flags, storage=storage, rounding="stochastic")
+        m0, _ = lat.totals()
+        lat.step(K)
+        m1, _ = lat.totals()
+        _, u = lat.moments_device()
+        lat.close()
+        err = (u - u_ref).abs().max().item() / umax
+        del u
+        assert err <= bound, f"{storage}, tau {tau}: velocity error {err:.3e}"
+        assert abs(m1 - m0) / m0 < 1e-4
+
+
+def _channel_error(dims, tau, steps, against_oracle):
+    """A forced duct of the serving stream (walls on the y and z faces,
+    g = 1e-6 along x, periodic x, started at rest): FP16 storage rounded
+    stochastically and to nearest against FP32 (and the FP64 oracle)."""
+    flags = W.channel_flags(*dims, walls=("y", "z"))
+    mask = flags == 0
+    u = {}
+    for name, storage, rounding in (("f32", "f32", "nearest"), ("sr", "f16s", "stochastic"),
+                                    ("rn", "f16s", "nearest")):
+        lat = Lattice(*dims, tau, flags=flags, storage=storage, force=(1e-6, 0.0, 0.0), rounding=rounding)
+        lat.step(steps)
+        u[name] = lat.moments()[1]
+        lat.close()
+    if against_oracle:
+        ora = O.Lattice(*dims, tau, flags=flags, force=(1e-6, 0.0, 0.0))
+        ora.step(steps)
+        u["oracle"] = ora.moments()[1]
+    return {k: vel_err(u[k], u["f32"], mask) for k in u if k != "f32"}, u, mask
+
+
+def test_forced_channel_request_f16_stochastic():
+    """The serving stream's 105 x 207 x 77 duct (tau 0.953, 4312 steps), whose
+    FP16 run rounded to nearest stalls (the force's increment is below half
+    an FP16 unit of the stored values): rounded stochastically it stays
+    within 2e-3 of the FP32 run."""
+    err, _, _ = _channel_error((105, 207, 77), 0.953, 4312, False)
+    assert err["sr"] <= 2e-3, err
+    assert err["rn"] > 1e-2, err  # the failure the rounding removes
+
+
+def test_forced_channel_f16_stochastic_vs_oracle():
+    """The same duct at half the size (52 x 104 x 38, tau 0.953, 4312 steps)
+    against the FP64 oracle: FP16 rounded stochastically within 2e-3, FP32
+    within 1e-5."""
+    err, u, mask = _channel_error((52, 104, 38), 0.953, 4312, True)
+    assert vel_err(u["sr"], u["oracle"], mask) <= 2e-3, err
+    assert vel_err(u["f32"], u["oracle"], mask) <= 1e-5
+
+
 @pytest.mark.parametrize("storage,tol", [("f16s", 2e-3), ("f32", 1e-5)])
 def test_cavity_64_vs_oracle(storage, tol):
     """The 64^3 copy of the precision case against the FP64 oracle, 1000

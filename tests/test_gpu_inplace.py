@@ -19,8 +19,8 @@ from paper_2409_16781_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-STORAGES = ["f64", "f32", "f16s", "bf16s", "f32d"]
-VEL_TOL = {"f32": 1e-5, "f16s": 2e-3, "bf16s": 3e-2, "f32d": 1e-6}
+STORAGES = ["f64", "f32", "f16s", "bf16s", "f32d", "e3m12s"]
+VEL_TOL = {"f32": 1e-5, "f16s": 2e-3, "bf16s": 3e-2, "f32d": 1e-6, "e3m12s": 5e-4}
 
 
 @pytest.fixture(scope="module")

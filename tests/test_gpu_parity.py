@@ -6,6 +6,8 @@ Tolerances (stated per storage form):
   f16s  : velocity, same measure, <= 2e-3
   bf16s : velocity, same measure, <= 3e-2 (reported form, 8-bit mantissa)
   f32d  : velocity, same measure, <= 1e-6 (FP32 storage, FP64 math)
+  e3m12s: velocity, same measure, <= 5e-4 (16-bit float with 12 mantissa bits:
+          a quarter of FP16's unit in the last place above 2^-10)
 """
 import numpy as np
 import pytest
@@ -17,7 +19,7 @@ from paper_2409_16781_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-VEL_TOL = {"f32": 1e-5, "f16s": 2e-3, "bf16s": 3e-2, "f32d": 1e-6}
+VEL_TOL = {"f32": 1e-5, "f16s": 2e-3, "bf16s": 3e-2, "f32d": 1e-6, "e3m12s": 5e-4}
 
 
 @pytest.fixture(scope="module")
@@ -57,7 +59,7 @@ def check_pair(ora, gpu, storage, perm, flags):
     assert np.all(rho_g[~mask] == 0) and np.all(u_g[:, ~mask] == 0)
 
 
-STORAGES = ["f64", "f32", "f16s", "bf16s", "f32d"]
+STORAGES = ["f64", "f32", "f16s", "bf16s", "f32d", "e3m12s"]
 
 TINY = [
     # nx, ny, nz, tau, steps, flags-spec, u_lid, force

@@ -9,7 +9,8 @@
   per step (exact for the update in exact arithmetic): within 1 % with
   stochastic rounding, while nearest rounding falls far short.
 * Against the FP64 oracle on the 64^3 cavity over 1000 steps the FP16 form
-  stays within the FP16S tolerance 2e-3 of max |u|.
+  stays within the FP16S tolerance 2e-3 of max |u|, the E3M12 form within
+  5e-4.
 """
 import numpy as np
 import pytest
@@ -43,7 +44,7 @@ def _run(storage, variant=0, steps=13, inplace=False, force=(3e-5, 0.0, 1e-5)):
     return lat
 
 
-@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+@pytest.mark.parametrize("storage", ["f16s", "bf16s", "e3m12s"])
 def test_every_variant_rounds_alike(storage):
     ref = _run(storage, 1).populations()
     for v in (0, 2, 3, 4, 6, 8, 13, 14, 15, 16, 17):
@@ -56,7 +57,7 @@ def test_every_variant_rounds_alike(storage):
             assert np.array_equal(a[:, fl], b[:, fl]), f"in place variant {v}, {steps} steps"
 
 
-@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+@pytest.mark.parametrize("storage", ["f16s", "bf16s", "e3m12s"])
 def test_stochastic_differs_from_nearest_and_is_reproducible(storage):
     a = _run(storage, 15).populations()
     b = _run(storage, 15).populations()
@@ -95,7 +96,7 @@ def test_batch_slot_equals_lattice_alone():
     assert np.array_equal(got, alone)
 
 
-@pytest.mark.parametrize("storage", ["f16s", "bf16s"])
+@pytest.mark.parametrize("storage", ["f16s", "bf16s", "e3m12s"])
 def test_weak_force_is_kept_on_average(storage):
     """Periodic box, all fluid, at rest, g = 2e-7 along x: the FP64 momentum
     grows by exactly mass * g per step in exact arithmetic."""
@@ -117,10 +118,11 @@ def test_cavity_64_against_oracle():
     ora = O.Lattice(n, n, n, 0.6, u_lid=(0.1, 0, 0), flags=fl)
     ora.step(steps)
     _, u_o = ora.moments()
-    lat = Lattice(n, n, n, 0.6, u_lid=(0.1, 0, 0), flags=fl, storage="f16s", rounding="stochastic")
-    lat.step(steps)
-    _, u_g = lat.moments()
-    assert vel_err(u_g, u_o, fluid_mask(fl, u_o.shape[1:])) <= 2e-3
+    for storage, tol in (("f16s", 2e-3), ("e3m12s", 5e-4)):
+        lat = Lattice(n, n, n, 0.6, u_lid=(0.1, 0, 0), flags=fl, storage=storage, rounding="stochastic")
+        lat.step(steps)
+        _, u_g = lat.moments()
+        assert vel_err(u_g, u_o, fluid_mask(fl, u_o.shape[1:])) <= tol, storage
 
 
 def test_rounding_needs_16_bit_storage():

@@ -29,7 +29,7 @@ class _Nothing:
     def __call__(self, local):
         pass
 
-    def sum(self, values, device="cpu"):
+    def sum(self, values):
         return np.asarray(values, dtype=np.float64)
 
 
@@ -74,7 +74,7 @@ def _ghosted_fields(s, rho, u):
     return ghosted(rho, s.z0, s.z1), ghosted(u, s.z0, s.z1, axis=1)
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16s", "bf16s", "f32d"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s", "bf16s", "f32d", "e3m12s"])
 @pytest.mark.parametrize("world", [2, 3])
 def test_slabs_equal_whole_lattice(storage, world):
     whole, slabs = _run(storage, 0, world, 7)

@@ -216,3 +216,37 @@ def test_per_request_jsonl_records(tmp_path):
         assert abs(l["latency_s"] - (l["finished_s"] - l["arrival_s"])) < 1e-5
         assert l["arrival_s"] <= l["admitted_s"] <= l["finished_s"]
     assert abs(np.percentile([l["latency_s"] for l in done], 50) - st.summary()["p50_s"]) < 1e-3
+
+
+def test_storage_policy_promotes_slowly_driven_16_bit_requests():
+    """A 16-bit request whose predicted deviations (U/6 for flow speed U) lie
+    below 2^-13 is served in FP32: FP16 keeps its 11 significant bits only
+    above 2^-14."""
+    from paper_2409_16781_gb300.serve import MIN_DEV_16, predicted_deviation, served_storage
+    assert MIN_DEV_16 == 2.0 ** -13
+    cav = W.Request(0, 0.0, 32, 32, 32, 0.6, 1000, "cavity", "f16s", u_lid=(0.05, 0.0, 0.0))
+    assert predicted_deviation(cav) == pytest.approx(0.05 / 6)
+    assert served_storage(cav) == "f16s"
+    # a narrow, viscous duct: its laminar centre speed g H^2 / (8 nu) bounds U
+    duct = W.Request(1, 0.0, 65, 54, 18, 0.978, 3115, "channel", "f16s", u_lid=(0.0, 0.0, 0.0),
+                     force=(1e-6, 0.0, 0.0))
+    nu, h = (0.978 - 0.5) / 3, 16
+    assert predicted_deviation(duct) == pytest.approx(1e-6 * h * h / (8 * nu) / 6)
+    assert served_storage(duct) == "f32"
+    assert served_storage(duct, promote=False) == "f16s"
+    # a wide duct: the free acceleration g t bounds U
+    wide = W.Request(2, 0.0, 105, 207, 77, 0.953, 4312, "channel", "f16s", u_lid=(0.0, 0.0, 0.0),
+                     force=(1e-6, 0.0, 0.0))
+    assert predicted_deviation(wide) == pytest.approx(1e-6 * 4312 / 6)
+    assert served_storage(wide) == "f16s"
+    fp32 = W.Request(3, 0.0, 8, 8, 8, 0.9, 200, "channel", "f32", force=(1e-6, 0.0, 0.0))
+    assert served_storage(fp32) == "f32"
+
+
+def test_scheduler_records_the_served_storage():
+    clock = VirtualClock()
+    be = FakeBackend(capacity=10 ** 9, slots=8, clock=clock)
+    be.storage_of = lambda req: "f32" if req.rid % 2 else req.storage
+    reqs = [W.Request(k, 0.0, 8, 8, 8, 0.7, 50, "cavity", "f16s") for k in range(4)]
+    st = Scheduler(be, clock=clock, sleep=clock.sleep).run(reqs)
+    assert sorted((r.rid, r.storage) for r in st.results) == [(0, "f16s"), (1, "f32"), (2, "f16s"), (3, "f32")]

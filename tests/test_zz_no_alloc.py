@@ -48,12 +48,12 @@ def _flags(nx, ny, nz):
 # Relative to the mass.  Against lb_totals (the same reduction kernel over
 # the same cells): 1e-12.  Against the FP64 oracle: 1e-12 for the forms with
 # FP64 arithmetic (f64, f32d); the forms with FP32 arithmetic (f32, f16s,
-# bf16s) sum each cell's 19 values in FP32 and take the far-field inflow and
+# bf16s, e3m12s) sum each cell's 19 values in FP32 and take the far-field inflow and
 # the lid term as FP32 constants, whose roundings have the same sign at every
 # cell of a boundary plane, so their totals sit within a few FP32 roundings
 # per boundary cell of the oracle's: 1e-8 of the mass.
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32d", 1e-12), ("f32", 1e-8),
-                                         ("f16s", 1e-8), ("bf16s", 1e-8)])
+                                         ("f16s", 1e-8), ("bf16s", 1e-8), ("e3m12s", 1e-8)])
 def test_static_totals_match_lb_totals_and_oracle(storage, tol):
     import torch
     lib = L.lib()
