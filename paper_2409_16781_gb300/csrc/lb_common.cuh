@@ -174,27 +174,36 @@ struct e3m12 {
     uint16_t v;
 };
 constexpr uint32_t E3M12_MAG_MAX = 0x03FFFFFFu;  // FP32 magnitude bits of the largest code (any low bits)
-__host__ __device__ inline uint32_t e3m12_bits(uint32_t code) {
-    return ((code & 0x8000u) << 16) | ((code & 0x7FFFu) << 11);
+// FP32 bit pattern of a code held in the high half of a word: an arithmetic
+// shift by 5 puts the magnitude at bits 25..11 and copies the sign into bits
+// 31..26, of which the mask keeps bit 31.
+__device__ __forceinline__ uint32_t e3m12_bits_hi(uint32_t w) {
+    return (uint32_t)((int32_t)w >> 5) & 0x83FFF800u;
 }
 __device__ __forceinline__ float e3m12_decode(uint32_t code) {
-    return __uint_as_float(e3m12_bits(code)) * 0x1p116f;
+    return __uint_as_float(e3m12_bits_hi(code << 16)) * 0x1p116f;
 }
 // the pair (low half, high half) of a 32-bit word as two FP32 values
 __device__ __forceinline__ float2 e3m12_decode2(uint32_t w) {
-    const float2 b = make_float2(__uint_as_float(e3m12_bits(w)),
-                                 __uint_as_float((w & 0x80000000u) | ((w >> 5) & 0x03FFF800u)));
+    const float2 b = make_float2(__uint_as_float(e3m12_bits_hi(w << 16)), __uint_as_float(e3m12_bits_hi(w)));
     return __fmul2_rn(b, make_float2(0x1p116f, 0x1p116f));
 }
-// add = increment to the magnitude below the kept bits (0 .. 0x7FF)
-__device__ __forceinline__ uint32_t e3m12_encode_add(float x, uint32_t add) {
-    const uint32_t b = __float_as_uint(x * 0x1p-116f);
-    const uint32_t m = min((b & 0x7FFFFFFFu) + add, E3M12_MAG_MAX);
-    return (m >> 11) | ((b >> 16) & 0x8000u);
+// Magnitude bits of |x| 2^-116 plus `add` (the rounding increment below the
+// kept 12 mantissa bits, 0 .. 0x7FF), clamped to the largest code.
+__device__ __forceinline__ uint32_t e3m12_mag(float x, uint32_t add) {
+    return min(__float_as_uint(fabsf(x) * 0x1p-116f) + add, E3M12_MAG_MAX);
 }
-__device__ __forceinline__ uint32_t e3m12_encode_rn(float x) {
-    const uint32_t m = __float_as_uint(x * 0x1p-116f) & 0x7FFFFFFFu;
-    return e3m12_encode_add(x, 0x3FFu + ((m >> 11) & 1u));
+__device__ __forceinline__ uint32_t e3m12_rn_add(float x) {
+    return 0x3FFu + ((__float_as_uint(fabsf(x) * 0x1p-116f) >> 11) & 1u);  // ties to the even code
+}
+__device__ __forceinline__ uint32_t e3m12_encode_add(float x, uint32_t add) {
+    return (e3m12_mag(x, add) >> 11) | ((__float_as_uint(x) >> 16) & 0x8000u);
+}
+__device__ __forceinline__ uint32_t e3m12_encode_rn(float x) { return e3m12_encode_add(x, e3m12_rn_add(x)); }
+// two codes packed as (lo | hi << 16)
+__device__ __forceinline__ uint32_t e3m12_encode2(float lo, float hi, uint32_t add_lo, uint32_t add_hi) {
+    const uint32_t mag = (e3m12_mag(lo, add_lo) >> 11) | ((e3m12_mag(hi, add_hi) << 5) & 0x7FFF0000u);
+    return mag | (__float_as_uint(hi) & 0x80000000u) | ((__float_as_uint(lo) >> 16) & 0x8000u);
 }
 template <> struct Storage<e3m12> {
     using math = float;
@@ -209,7 +218,7 @@ constexpr bool ieee16 = std::is_same<S, __half>::value || std::is_same<S, __nv_b
 // stochastic rounding of an E3M12 pair: the low half takes bits[10:0], the
 // high half bits[31:21] (each cell's own bits, as for the IEEE forms)
 template <> __device__ __forceinline__ uint32_t cvt_rs2<e3m12>(float lo, float hi, uint32_t bits) {
-    return e3m12_encode_add(lo, bits & 0x7FFu) | (e3m12_encode_add(hi, bits >> 21) << 16);
+    return e3m12_encode2(lo, hi, bits & 0x7FFu, bits >> 21);
 }
 
 // Parameters of one lattice as seen by the kernels.
@@ -237,6 +246,13 @@ struct LatticeParams {
     // fields in every thread (a GB300 runs that conversion on its narrow
     // FP64 pipe); the rounding is the same, so the results are too.
     float omega_f, omega_m_f, g_f[3];
+    // per-lattice constants of the collision, also computed on the host
+    // (set_farfield) so that no thread recomputes them: half the force
+    // (the velocity shift), (1 - omega)/2 and (1 - omega_m)/2 (the pair
+    // sums' and differences' own share), 1 - omega/2 and 1 - omega_m/2 (the
+    // Guo prefactors), each exactly as a thread would round it
+    double gh[3], omh, omh_m, pref, pref_m;
+    float gh_f[3], omh_f, omh_m_f, pref_f, pref_m_f;
 };
 
 // A lattice parameter in the arithmetic type M: the FP64 field for FP64
@@ -255,7 +271,21 @@ __host__ __device__ __forceinline__ M param(double d, float f) {
 inline void set_farfield(LatticeParams& p) {
     p.omega_f = (float)p.omega;
     p.omega_m_f = (float)p.omega_m;
-    for (int a = 0; a < 3; ++a) p.g_f[a] = (float)p.g[a];
+    for (int a = 0; a < 3; ++a) {
+        p.g_f[a] = (float)p.g[a];
+        p.gh[a] = 0.5 * p.g[a];      // exact
+        p.gh_f[a] = 0.5f * p.g_f[a];  // exact
+    }
+    // each a product by 1/2 (exact) and one rounded sum, in the precision
+    // that uses it
+    p.omh = 0.5 - 0.5 * p.omega;
+    p.omh_m = 0.5 - 0.5 * p.omega_m;
+    p.pref = 1.0 - 0.5 * p.omega;
+    p.pref_m = 1.0 - 0.5 * p.omega_m;
+    p.omh_f = 0.5f - 0.5f * p.omega_f;
+    p.omh_m_f = 0.5f - 0.5f * p.omega_m_f;
+    p.pref_f = 1.0f - 0.5f * p.omega_f;
+    p.pref_m_f = 1.0f - 0.5f * p.omega_m_f;
     const double uu = p.ulid[0] * p.ulid[0] + p.ulid[1] * p.ulid[1] + p.ulid[2] * p.ulid[2];
     for (int i = 0; i < 19; ++i) {
         const double cu = D3Q19::cx(i) * p.ulid[0] + D3Q19::cy(i) * p.ulid[1] + D3Q19::cz(i) * p.ulid[2];

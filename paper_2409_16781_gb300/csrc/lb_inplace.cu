@@ -23,6 +23,28 @@
 
 namespace lbgb {
 
+// One stored value of the neighbouring lane (up: lane - 1, else lane + 1),
+// and the helpers that pack two stored values into one aligned store.
+template <class S>
+__device__ __forceinline__ uint16_t bits16(S v) {
+    static_assert(sizeof(S) == 2, "16-bit storage");
+    return *reinterpret_cast<const uint16_t*>(&v);
+}
+template <class S>
+__device__ __forceinline__ S shfl_val(S v, bool up) {
+    if constexpr (sizeof(S) == 2) {
+        const uint32_t w = bits16(v);
+        const uint32_t r = up ? __shfl_up_sync(0xffffffffu, w, 1) : __shfl_down_sync(0xffffffffu, w, 1);
+        return from_bits16<S>(r);
+    } else {
+        return up ? __shfl_up_sync(0xffffffffu, v, 1) : __shfl_down_sync(0xffffffffu, v, 1);
+    }
+}
+template <class S>
+__device__ __forceinline__ typename Vec2<S>::T pack_vals(S a, S b) {
+    return typename Vec2<S>::T{a, b};
+}
+
 // Ar and Aw are the same array.  They come in as two pointers (neither
 // restrict-qualified, so the compiler keeps every load before the stores that
 // follow it) only so that the compiler does not keep the 19 load addresses
@@ -104,10 +126,15 @@ __global__ void __launch_bounds__(128, 8) step_kernel_inplace_pairs(const S* Ar,
             }
         }
     }
-    if (!active) return;
     const uint8_t c0 = code[cell0], c1 = code[cell0 + 1];
-    const bool f0 = !(c0 & CODE_TYPE), f1 = !(c1 & CODE_TYPE);
-    if (!f0 && !f1) return;  // solid cells hold no values of their own
+    // what this lane stores: solid cells hold no values of their own, idle
+    // lanes nothing
+    const bool f0 = active && !(c0 & CODE_TYPE), f1 = active && !(c1 & CODE_TYPE);
+    if constexpr (FORM == FORM_STREAMED) {
+        if (!f0 && !f1) return;
+    }
+    // (from the swapped layout every lane goes on: its stores below trade
+    // values with the neighbouring lanes)
     bounce_fix_x2<S, 0, FORM>(Ar, code, p, x0, y, z, cell0, c0, c1, d);
     relax_dev<f32x2, FORCE>(d, p);
     // each value is rounded by the cell that computed it (cell0 or
@@ -135,9 +162,30 @@ __global__ void __launch_bounds__(128, 8) step_kernel_inplace_pairs(const S* Ar,
             }
         }
     } else {
-        // -> FORM_STREAMED: P_i(x) into plane i at x + c_i (periodic wrap)
+        // -> FORM_STREAMED: P_i(x) into plane i at x + c_i (periodic wrap).
+        // A direction with c_x = +-1 moves both values of the pair one slot
+        // along x, out of the pair's alignment: the aligned slots (x0, x0+1)
+        // then take one value of this lane and one of the neighbouring lane
+        // (a shuffle), so each lane still issues one aligned pair store; at
+        // a warp or row edge a lane stores its outgoing value on its own.
         const int yt[3] = {(y == 0 ? ny - 1 : y - 1) * nx, y * nx, (y == ny - 1 ? 0 : y + 1) * nx};
         const int zt[3] = {(z == 0 ? nz - 1 : z - 1) * nxy, z * nxy, (z == nz - 1 ? 0 : z + 1) * nxy};
+        const bool has_prev = lane != 0 && x0 != 0;      // the previous lane holds pair x0 - 2
+        const bool has_next = lane != 31 && x0 + 2 < nx;  // the next lane holds pair x0 + 2
+        const bool p1 = __shfl_up_sync(0xffffffffu, f1, 1);
+        const bool n0 = __shfl_down_sync(0xffffffffu, f0, 1);
+        // the two values of slots (x0, x0+1), written where each is fluid
+        auto put = [&](S* q, S a, S b, bool fa, bool fb) {
+            if (fa && fb) {
+                if constexpr (sizeof(S) == 2)
+                    st_pop<0>(reinterpret_cast<uint32_t*>(q), (uint32_t)bits16(a) | ((uint32_t)bits16(b) << 16));
+                else
+                    st_pop<0>(reinterpret_cast<V*>(q), pack_vals<S>(a, b));
+            } else {
+                if (fa) st_pop<0>(q, a);
+                if (fb) st_pop<0>(q + 1, b);
+            }
+        };
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             S* rowt = Aw + (int64_t)i * p.ps + yt[D3Q19::cy(i) + 1] + zt[D3Q19::cz(i) + 1];
@@ -148,12 +196,19 @@ __global__ void __launch_bounds__(128, 8) step_kernel_inplace_pairs(const S* Ar,
                     if (f0) st_pop<0>(rowt + x0, R.one(d[i].v.x, key, cell0, i));
                     if (f1) st_pop<0>(rowt + x0 + 1, R.one(d[i].v.y, key, cell0 + 1, i));
                 }
-            } else if (D3Q19::cx(i) == 1) {  // targets x0 + 1, x0 + 2
-                if (f0) st_pop<0>(rowt + x0 + 1, R.one(d[i].v.x, key, cell0, i));
-                if (f1) st_pop<0>(rowt + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2), R.one(d[i].v.y, key, cell0 + 1, i));
-            } else {  // targets x0 - 1, x0
-                if (f0) st_pop<0>(rowt + (x0 == 0 ? nx - 1 : x0 - 1), R.one(d[i].v.x, key, cell0, i));
-                if (f1) st_pop<0>(rowt + x0, R.one(d[i].v.y, key, cell0 + 1, i));
+                continue;
+            }
+            const S v0 = R.one(d[i].v.x, key, cell0, i), v1 = R.one(d[i].v.y, key, cell0 + 1, i);
+            if (D3Q19::cx(i) == 1) {  // x0 -> x0 + 1, x0 + 1 -> x0 + 2
+                const S pv = shfl_val<S>(v1, true);  // the previous lane's x0 - 1 -> x0
+                if (has_prev) put(rowt + x0, pv, v0, p1, f0);
+                else if (f0) st_pop<0>(rowt + x0 + 1, v0);
+                if (!has_next && f1) st_pop<0>(rowt + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2), v1);
+            } else {  // x0 -> x0 - 1, x0 + 1 -> x0
+                const S nv = shfl_val<S>(v0, false);  // the next lane's x0 + 2 -> x0 + 1
+                if (has_next) put(rowt + x0, v1, nv, f1, n0);
+                else if (f1) st_pop<0>(rowt + x0, v1);
+                if (!has_prev && f0) st_pop<0>(rowt + (x0 == 0 ? nx - 1 : x0 - 1), v0);
             }
         }
     }

@@ -329,11 +329,24 @@ __device__ __forceinline__ f32x2 fmad(f32x2 a, f32x2 b, f32x2 c) {
     return r;
 }
 
-// 1/rho, correctly rounded.  An approximate reciprocal is not good enough:
-// its error has a sign bias, so the equilibrium momentum rho u falls short
-// of j by a fixed fraction every step and the collision drains momentum
-// (an artificial dissipation that builds up over thousands of steps).
-__device__ __forceinline__ double recip(double r) { return 1.0 / r; }
+// 1/rho.  FP32: correctly rounded -- the hardware approximation's error has
+// a sign bias, so the equilibrium momentum rho u would fall short of j by a
+// fixed fraction every step and the collision would drain momentum (an
+// artificial dissipation that builds up over thousands of steps).  FP64:
+// the hardware's approximate reciprocal refined by two Newton steps
+// y <- y + y (1 - r y), each squaring the relative error, so the result is
+// within about one unit in the last place of 1/r -- three orders of
+// magnitude below the FP32 bias -- for a fraction of the FP64 instructions
+// of the IEEE division (the FP64 pipe bounds the FP64 forms).  Densities
+// are near 1, far from the approximation's subnormal and overflow limits.
+__device__ __forceinline__ double recip(double r) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(r));
+    double e = __fma_rn(-r, y, 1.0);
+    y = __fma_rn(y, e, y);
+    e = __fma_rn(-r, y, 1.0);
+    return __fma_rn(y, e, y);
+}
 __device__ __forceinline__ float recip(float r) { return __frcp_rn(r); }
 __device__ __forceinline__ f32x2 recip(f32x2 r) { return f32x2(__frcp_rn(r.v.x), __frcp_rn(r.v.y)); }
 
@@ -345,9 +358,9 @@ __device__ __forceinline__ void macro_dev(const M (&d)[Q], const LatticeParams& 
     moment_sums<M>(d, drho, jx, jy, jz);
     rho = M(1) + drho;
     const M inv = recip(rho);
-    ux = fmad(jx, inv, M(0.5) * param<M>(p.g[0], p.g_f[0]));
-    uy = fmad(jy, inv, M(0.5) * param<M>(p.g[1], p.g_f[1]));
-    uz = fmad(jz, inv, M(0.5) * param<M>(p.g[2], p.g_f[2]));
+    ux = fmad(jx, inv, param<M>(p.gh[0], p.gh_f[0]));
+    uy = fmad(jy, inv, param<M>(p.gh[1], p.gh_f[1]));
+    uz = fmad(jz, inv, param<M>(p.gh[2], p.gh_f[2]));
 }
 
 // BGK relaxation towards f^eq (Eq. 2-3) plus the Guo source term (the S_i
@@ -398,9 +411,17 @@ __device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams&
     }
     const M rho = M(1) + drho;
     const M inv = recip(rho);
-    const M ux = fmad(jx, inv, M(0.5) * param<M>(p.g[0], p.g_f[0]));
-    const M uy = fmad(jy, inv, M(0.5) * param<M>(p.g[1], p.g_f[1]));
-    const M uz = fmad(jz, inv, M(0.5) * param<M>(p.g[2], p.g_f[2]));
+    // u = j / rho + g / 2 (without a force: j / rho)
+    M ux, uy, uz;
+    if constexpr (FORCE) {
+        ux = fmad(jx, inv, param<M>(p.gh[0], p.gh_f[0]));
+        uy = fmad(jy, inv, param<M>(p.gh[1], p.gh_f[1]));
+        uz = fmad(jz, inv, param<M>(p.gh[2], p.gh_f[2]));
+    } else {
+        ux = jx * inv;
+        uy = jy * inv;
+        uz = jz * inv;
+    }
     const M om = param<M>(p.omega, p.omega_f);
     const M omm = param<M>(p.omega_m, p.omega_m_f);
     const M uu15 = M(1.5) * fmad(ux, ux, fmad(uy, uy, uz * uz));
@@ -410,8 +431,8 @@ __device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams&
         Fy = rho * param<M>(p.g[1], p.g_f[1]);
         Fz = rho * param<M>(p.g[2], p.g_f[2]);
         uF = fmad(ux, Fx, fmad(uy, Fy, uz * Fz));
-        pref = fmad(M(-0.5), om, M(1));
-        pref_m = fmad(M(-0.5), omm, M(1));
+        pref = param<M>(p.pref, p.pref_f);
+        pref_m = param<M>(p.pref_m, p.pref_m_f);
     }
     // Half the post-collision pair sums (hs) and differences (hd):
     //   hs = (1 - omega)/2 (d_i + d_i') + even,   hd = (1 - omega_m)/2 (d_i - d_i') + odd,
@@ -419,8 +440,8 @@ __device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams&
     //   even = omega W (rho (4.5 cu^2 - 1.5 uu) + drho) [+ pref W (9 cu cF - 3 uF)]
     //   odd  = 3 omega_m W rho cu                       [+ 3 pref_m W cF]
     const M wa = (M)D3Q19::w(1), wb = (M)D3Q19::w(7);
-    const M omh = fmad(M(-0.5), om, M(0.5));
-    const M omh_m = fmad(M(-0.5), omm, M(0.5));
+    const M omh = param<M>(p.omh, p.omh_f);
+    const M omh_m = param<M>(p.omh_m, p.omh_m_f);
     const M orho = om * rho;
     const M base = om * fmad(rho, -uu15, drho);
     const M a1 = M(4.5) * wa * orho, b1 = wa * base;
@@ -489,9 +510,9 @@ __device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams&
         emit(i + 1, hs - hd);
     }
     // axis pairs (1,2) x, (3,4) y, (5,6) z: post-collision momentum j + F
-    const M hdx = fmad(M(0.5), jx + Fx, -ox);
-    const M hdy = fmad(M(0.5), jy + Fy, -oy);
-    const M hdz = fmad(M(0.5), jz + Fz, -oz);
+    const M hdx = fmad(M(0.5), FORCE ? jx + Fx : jx, -ox);
+    const M hdy = fmad(M(0.5), FORCE ? jy + Fy : jy, -oy);
+    const M hdz = fmad(M(0.5), FORCE ? jz + Fz : jz, -oz);
     emit(1, hsa[0] + hdx);
     emit(2, hsa[0] - hdx);
     emit(3, hsa[1] + hdy);
@@ -551,7 +572,7 @@ struct Rounder {
             const __half2 h = __floats2half2_rn(lo, hi);
             return *reinterpret_cast<const uint32_t*>(&h);
         } else if constexpr (std::is_same<S, e3m12>::value) {
-            return e3m12_encode_rn(lo) | (e3m12_encode_rn(hi) << 16);
+            return e3m12_encode2(lo, hi, e3m12_rn_add(lo), e3m12_rn_add(hi));
         } else {
             const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
             return *reinterpret_cast<const uint32_t*>(&h);

@@ -49,7 +49,7 @@ template <> __device__ __forceinline__ __nv_bfloat162 pack2<__nv_bfloat16>(float
 }
 
 template <> __device__ __forceinline__ uint32_t pack2<e3m12>(float a, float b) {
-    return e3m12_encode_rn(a) | (e3m12_encode_rn(b) << 16);
+    return e3m12_encode2(a, b, e3m12_rn_add(a), e3m12_rn_add(b));
 }
 
 template <class S> __device__ __forceinline__ f32x2 to_x2(uint32_t w);  // two packed 16-bit values

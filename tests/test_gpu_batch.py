@@ -220,6 +220,7 @@ class _CountingBackend(BatchBackend):
         self.grants = {}
         self.slot_rid = {}
         self.chunk = 0
+        self.clock = None
 
     def admit(self, req):
         h = super().admit(req)
@@ -237,18 +238,39 @@ class _CountingBackend(BatchBackend):
     def step(self, n):
         super().step(n)
         self.chunk += 1
+        if self.clock is not None:
+            self.clock.t += 1e-3
+
+
+class _ChunkClock:
+    """Scheduler time that advances 1 ms per issued chunk (and by the sleeps
+    of an idle scheduler), so that which request arrives during which chunk
+    -- and so the whole schedule -- does not depend on the host's speed."""
+
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += max(dt, 1e-6)
 
 
 @pytest.mark.parametrize("rounding", ["nearest", "stochastic"])
 def test_serve_chunked_quotas_and_pauses_same_as_alone(rounding):
     """Through serve() with the srpt policy: every request is granted its
     steps in at least 3 chunks (max_chunk caps a chunk), some requests are
-    paused (quota 0) between grants while others run, and each result
-    equals the request run alone element by element."""
+    paused (left without a quota) between grants while shorter ones that
+    arrived later run, and each result equals the request run alone element
+    by element."""
     reqs = W.request_stream(n=12, rate_hz=400.0, seed=7, min_cells=6 ** 3, max_cells=18 ** 3,
                             steps_range=(60, 160))
+    clock = _ChunkClock()
     be = _CountingBackend(capacity_bytes=128 << 20, max_slots=12, keep_fields=True, rounding=rounding)
-    st = serve(reqs, be, chunk_ms=1.0, policy="srpt", target_cells=3000, max_chunk=16, min_chunk=4)
+    be.clock = clock
+    st = serve(reqs, be, chunk_ms=1.0, policy="srpt", target_cells=3000, max_chunk=16, min_chunk=4,
+               clock=clock, sleep=clock.sleep)
     be.close()
     assert len(st.results) == len(reqs) and not st.rejected
     paused_between = 0

@@ -85,7 +85,7 @@ def test_batch_pool_stays_inside_its_buffer():
     ragged shapes) stepping in shared launches writes only inside its pool."""
     import torch
     lib = L.lib()
-    max_slots = 32
+    max_slots = 40
     fixed = int(lib.lb_batch_fixed_bytes(max_slots))
     cap = 64 << 20
     nbytes = fixed + cap
