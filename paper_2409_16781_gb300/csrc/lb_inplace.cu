@@ -198,17 +198,43 @@ __global__ void __launch_bounds__(128, 8) step_kernel_inplace_pairs(const S* Ar,
                 }
                 continue;
             }
-            const S v0 = R.one(d[i].v.x, key, cell0, i), v1 = R.one(d[i].v.y, key, cell0 + 1, i);
-            if (D3Q19::cx(i) == 1) {  // x0 -> x0 + 1, x0 + 1 -> x0 + 2
-                const S pv = shfl_val<S>(v1, true);  // the previous lane's x0 - 1 -> x0
-                if (has_prev) put(rowt + x0, pv, v0, p1, f0);
-                else if (f0) st_pop<0>(rowt + x0 + 1, v0);
-                if (!has_next && f1) st_pop<0>(rowt + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2), v1);
-            } else {  // x0 -> x0 - 1, x0 + 1 -> x0
-                const S nv = shfl_val<S>(v0, false);  // the next lane's x0 + 2 -> x0 + 1
-                if (has_next) put(rowt + x0, v1, nv, f1, n0);
-                else if (f1) st_pop<0>(rowt + x0, v1);
-                if (!has_prev && f0) st_pop<0>(rowt + (x0 == 0 ? nx - 1 : x0 - 1), v0);
+            if constexpr (sizeof(S) == 2) {
+                // both values rounded into one word (low half: cell x0), which
+                // then travels between lanes as a whole
+                const uint32_t w = R.two(d[i].v.x, d[i].v.y, key, i);
+                const S v0 = from_bits16<S>(w & 0xffffu), v1 = from_bits16<S>(w >> 16);
+                if (D3Q19::cx(i) == 1) {  // x0 -> x0 + 1, x0 + 1 -> x0 + 2
+                    const uint32_t pw = __shfl_up_sync(0xffffffffu, w, 1);
+                    if (has_prev) {  // slots (x0, x0 + 1) <- (previous lane's x0 - 1, x0)
+                        if (p1 && f0) st_pop<0>(reinterpret_cast<uint32_t*>(rowt + x0), __byte_perm(pw, w, 0x5432));
+                        else put(rowt + x0, from_bits16<S>(pw >> 16), v0, p1, f0);
+                    } else if (f0) {
+                        st_pop<0>(rowt + x0 + 1, v0);
+                    }
+                    if (!has_next && f1) st_pop<0>(rowt + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2), v1);
+                } else {  // x0 -> x0 - 1, x0 + 1 -> x0
+                    const uint32_t nw = __shfl_down_sync(0xffffffffu, w, 1);
+                    if (has_next) {  // slots (x0, x0 + 1) <- (x0 + 1, next lane's x0 + 2)
+                        if (f1 && n0) st_pop<0>(reinterpret_cast<uint32_t*>(rowt + x0), __byte_perm(w, nw, 0x5432));
+                        else put(rowt + x0, v1, from_bits16<S>(nw & 0xffffu), f1, n0);
+                    } else if (f1) {
+                        st_pop<0>(rowt + x0, v1);
+                    }
+                    if (!has_prev && f0) st_pop<0>(rowt + (x0 == 0 ? nx - 1 : x0 - 1), v0);
+                }
+            } else {
+                const S v0 = R.one(d[i].v.x, key, cell0, i), v1 = R.one(d[i].v.y, key, cell0 + 1, i);
+                if (D3Q19::cx(i) == 1) {  // x0 -> x0 + 1, x0 + 1 -> x0 + 2
+                    const S pv = shfl_val<S>(v1, true);  // the previous lane's x0 - 1 -> x0
+                    if (has_prev) put(rowt + x0, pv, v0, p1, f0);
+                    else if (f0) st_pop<0>(rowt + x0 + 1, v0);
+                    if (!has_next && f1) st_pop<0>(rowt + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2), v1);
+                } else {  // x0 -> x0 - 1, x0 + 1 -> x0
+                    const S nv = shfl_val<S>(v0, false);  // the next lane's x0 + 2 -> x0 + 1
+                    if (has_next) put(rowt + x0, v1, nv, f1, n0);
+                    else if (f1) st_pop<0>(rowt + x0, v1);
+                    if (!has_prev && f0) st_pop<0>(rowt + (x0 == 0 ? nx - 1 : x0 - 1), v0);
+                }
             }
         }
     }

@@ -393,15 +393,22 @@ __device__ __forceinline__ void macro_dev(const M (&d)[Q], const LatticeParams& 
 // in registers; relax_dev writes them back into d.
 template <class M, bool FORCE, class Emit>
 __device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams& p, Emit&& emit) {
-    // pre-collision pair sums / differences and moments
+    // pre-collision pair sums / differences and moments (the axis pairs
+    // (1,2), (3,4), (5,6) start j along +x, +y, +z; the diagonal pairs add
+    // to it, so no sum starts from a zero)
     M ps[9], pd[9];
-    M drho = d[0], jx = 0, jy = 0, jz = 0;
+    M drho = d[0];
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
         const int i = 2 * k + 1;
         ps[k] = d[i] + d[i + 1];
         pd[k] = d[i] - d[i + 1];
         drho += ps[k];
+    }
+    M jx = pd[0], jy = pd[1], jz = pd[2];
+#pragma unroll
+    for (int k = 3; k < 9; ++k) {
+        const int i = 2 * k + 1;
         if (D3Q19::cx(i) == 1) jx += pd[k];
         if (D3Q19::cx(i) == -1) jx -= pd[k];
         if (D3Q19::cy(i) == 1) jy += pd[k];
@@ -487,7 +494,17 @@ __device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams&
         hsa[k] = fmad(omh, ps[k], even);
     }
     M msum = hsa[0] + hsa[1] + hsa[2];
-    M ox = 0, oy = 0, oz = 0;  // half the momentum carried by the 12 diagonal directions
+    // half the momentum carried by the 12 diagonal directions; each sum
+    // starts at its first term (the flags fold away once the loop is unrolled)
+    M ox = 0, oy = 0, oz = 0;
+    bool fx = true, fy = true, fz = true;
+    auto acc = [](M& o, bool& first, int c, M v) {
+        if (c == 0) return;
+        if (first) o = c > 0 ? v : -v;
+        else if (c > 0) o += v;
+        else o -= v;
+        first = false;
+    };
 #pragma unroll
     for (int k = 3; k < 9; ++k) {
         const int i = 2 * k + 1;
@@ -499,12 +516,9 @@ __device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams&
         M odd = c2 * cu;
         if (FORCE) odd = fmad(fc2, cF, odd);
         const M hd = fmad(omh_m, pd[k], odd);
-        if (D3Q19::cx(i) == 1) ox += hd;
-        if (D3Q19::cx(i) == -1) ox -= hd;
-        if (D3Q19::cy(i) == 1) oy += hd;
-        if (D3Q19::cy(i) == -1) oy -= hd;
-        if (D3Q19::cz(i) == 1) oz += hd;
-        if (D3Q19::cz(i) == -1) oz -= hd;
+        acc(ox, fx, D3Q19::cx(i), hd);
+        acc(oy, fy, D3Q19::cy(i), hd);
+        acc(oz, fz, D3Q19::cz(i), hd);
         msum += hs;
         emit(i, hs + hd);
         emit(i + 1, hs - hd);
