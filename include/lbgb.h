@@ -247,7 +247,9 @@ int lb_get_populations_at(lb_lattice *h, const int64_t *cells, int n, double *ou
 int lb_set_kernel(lb_lattice *h, int variant, int block);
 
 /* Autotuner: time every applicable (variant, block) pair on this lattice
- * with `reps` launches each (CUDA events on the lattice's stream), keep the
+ * (the TMA pipeline variants 10-12 excepted: slower than the register
+ * kernels on every lattice measured on GB300; lb_set_kernel still selects
+ * them) with `reps` launches each (CUDA events on the lattice's stream), keep the
  * fastest for later lb_step calls and report it (outputs may be NULL).
  * The timed launches read array A and write array B only, so the lattice
  * state is unchanged.  An in-place lattice has no second array: its

@@ -613,11 +613,8 @@ int lb_autotune(lb_lattice* h, int reps, int* variant, int* block, float* ms_per
     if (h->walls) {
         for (int b : {64, 128}) add(16, b);
     }
-    if (sixteen && h->nx % 16 == 0 && all) {
-        add(10, 0);
-        add(11, 0);
-        add(12, 0);
-    }
+    // (the TMA pipeline variants 10-12 are not tried: slower than the
+    // register kernels on every lattice measured on GB300)
     const LatticeParams p = params_of(h);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return cuda_fail(cudaGetLastError(), "lb_autotune: event");
