@@ -181,7 +181,19 @@ class ClockSampler:
         self.gpu = gpu_index
         self.enabled = enabled
         self.proc = None
-        self.lines = []
+        self.lines = []          # (host monotonic time of arrival, line)
+        self.window = None       # (start, end) of the timed region, host monotonic
+        self.continued = False   # the window is the same load continued after a short region
+
+    def mark(self, start: bool):
+        """Note the host time at which the timed region starts / ends (the
+        sampler runs from before the warm-up so that it is already sampling
+        when a short region starts)."""
+        t = time.monotonic()
+        if start:
+            self.window = (t, None)
+        elif self.window is not None:
+            self.window = (self.window[0], t)
 
     def start(self):
         if not self.enabled:
@@ -198,7 +210,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
 
     def stop(self):
         if self.proc is None:
@@ -214,7 +226,21 @@ class ClockSampler:
     def summary(self):
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        lines = self.lines
+        where = "whole run"
+        if self.window is not None and self.window[1] is not None:
+            # samples taken during the region (one sampling period of slack at
+            # the end); a region shorter than the period gets the first
+            # sample after it started
+            t0, t1 = self.window
+            lines = [(t, ln) for t, ln in self.lines if t0 <= t <= t1 + 0.05]
+            where = ("the same steps continued untimed for 0.5 s right after the timed region (shorter "
+                     "than the 100 ms sampling period)" if self.continued else "timed region")
+            if not lines:
+                after = [(t, ln) for t, ln in self.lines if t >= t0]
+                lines = after[:1]
+                where = "first sample after the window started"
+        for _, ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -229,7 +255,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "sampled": where}
 
 
 # ---------------------------------------------------------------- helpers
@@ -400,6 +426,8 @@ def run_ours(args, dist: Dist):
         return slab.totals() if slab is not None else lat.totals()
 
     launches_per_check = 2  # reduction kernel + finalize kernel
+    clocks = ClockSampler(dist.local_rank, enabled=not args.no_clocks and dist.local_rank == 0)
+    clocks.start()  # already sampling when the timed region starts
     for _ in range(args.warmup):
         step()
     totals()
@@ -409,11 +437,10 @@ def run_ours(args, dist: Dist):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(dist.local_rank, enabled=not args.no_clocks and dist.local_rank == 0)
     n_checks = 0
     dist.barrier()
     torch.cuda.synchronize(dev)
-    clocks.start()
+    clocks.mark(True)
     t_start.record(stream)
     for k in range(K):
         ev[k][0].record(stream)
@@ -428,9 +455,22 @@ def run_ours(args, dist: Dist):
     n_checks += 1
     t_end.record(stream)
     torch.cuda.synchronize(dev)
+    clocks.mark(False)
+    seconds = t_start.elapsed_time(t_end) / 1e3
+    if clocks.enabled and seconds < 0.5:
+        # a region shorter than a few 100 ms sampling periods: keep the same
+        # load (untimed step launches, no halo exchange, so that no other rank
+        # takes part; the state is re-initialised by the e2e run below) for
+        # about half a second and sample that
+        extra = int(math.ceil(0.5 / max(seconds / K, 1e-6)))
+        clocks.mark(True)
+        for _ in range(extra):
+            lat.step(1)
+        torch.cuda.synchronize(dev)
+        clocks.mark(False)
+        clocks.continued = True
     dist.barrier()
     clock_summary = clocks.stop()
-    seconds = t_start.elapsed_time(t_end) / 1e3
     step_ms = [a.elapsed_time(b) for a, b in ev]
     kernel_ms = statistics.mean(step_ms)
     value, t_max = aggregate_replicas(dist, N, K, seconds)
