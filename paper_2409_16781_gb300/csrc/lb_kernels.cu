@@ -126,8 +126,11 @@ constexpr int TOT_THREADS = 256;
 constexpr int TOT_FOLD = 8;
 constexpr int TOT_PARTS = 6;
 
+// At most 64 registers (4 blocks of TOT_THREADS per SM): uncapped, the 19
+// pulled values, the sums and the FP64 accumulators took 97 registers, two
+// blocks per SM, and the reduction ran at well under half the bandwidth.
 template <class S, int FORM, bool FLAGS = false>
-__global__ void __launch_bounds__(TOT_THREADS) totals_kernel(const S* __restrict__ A,
+__global__ void __launch_bounds__(TOT_THREADS, 4) totals_kernel(const S* __restrict__ A,
                                                              const uint8_t* __restrict__ code,
                                                              LatticeParams p, double* __restrict__ partials) {
     using M = typename Storage<S>::math;

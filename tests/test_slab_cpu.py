@@ -126,3 +126,20 @@ def test_slabs_over_gloo_ranks_equal_the_whole_lattice(world):
         p.join(timeout=60)
         assert p.exitcode == 0
     _check(results)
+
+
+def test_bench_slab_inputs_are_the_ghosted_global_fields():
+    """bench.py builds each z-slab's Taylor-Green fields without the whole
+    lattice's arrays: they must equal the ghosted slices of the global ones."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2409_16781_gb300 import workloads as W
+    from paper_2409_16781_gb300.slab import ghosted, slab_range
+    n, world = 12, 3
+    nz = n * world
+    rho, u = W.taylor_green_fields(n, n, nz, u0=0.05)
+    for r in range(world):
+        z0, z1 = slab_range(nz, world, r)
+        rl, ul = bench.tgv_slab_inputs(n, nz, z0, z1)
+        assert np.allclose(rl, ghosted(rho, z0, z1), rtol=0, atol=0)
+        assert np.allclose(ul, ghosted(u, z0, z1, axis=1), rtol=0, atol=1e-15)
