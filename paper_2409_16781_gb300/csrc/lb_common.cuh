@@ -253,6 +253,7 @@ struct LatticeParams {
     // Guo prefactors), each exactly as a thread would round it
     double gh[3], omh, omh_m, pref, pref_m;
     float gh_f[3], omh_f, omh_m_f, pref_f, pref_m_f;
+    double om1;  // 1 - omega (the FP64 rest population's own share)
 };
 
 // A lattice parameter in the arithmetic type M: the FP64 field for FP64
@@ -280,6 +281,7 @@ inline void set_farfield(LatticeParams& p) {
     // that uses it
     p.omh = 0.5 - 0.5 * p.omega;
     p.omh_m = 0.5 - 0.5 * p.omega_m;
+    p.om1 = 1.0 - p.omega;
     p.pref = 1.0 - 0.5 * p.omega;
     p.pref_m = 1.0 - 0.5 * p.omega_m;
     p.omh_f = 0.5f - 0.5f * p.omega_f;

@@ -387,12 +387,20 @@ __device__ __forceinline__ void macro_dev(const M (&d)[Q], const LatticeParams& 
 // M is double, float, or f32x2 (two cells at once); every multiply-add is an
 // explicit fmad, so the packed form rounds each cell as the scalar form does.
 //
+// FP64 arithmetic (M = double) takes the axis pairs' differences and the
+// rest population from the equilibrium directly, as the diagonal pairs do:
+// there the rounded weights move mass and momentum by parts in 1e16 per
+// step, far below anything the solutions resolve, while the closure's sums
+// cost 12 instructions per cell on the FP64 pipe that bounds the FP64 forms.
+//
 // relax_emit hands each post-collision value to emit(i, value) as soon as it
-// is final (the diagonal pairs first, then the axis pairs, then the rest
-// population), so a kernel can store it at once instead of keeping all 19
-// in registers; relax_dev writes them back into d.
+// is final (FP32: the diagonal pairs first, then the axis pairs, then the
+// rest population; FP64: the axis pairs, the diagonal pairs, the rest), so a
+// kernel can store it at once instead of keeping all 19 in registers;
+// relax_dev writes them back into d.
 template <class M, bool FORCE, class Emit>
 __device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams& p, Emit&& emit) {
+    constexpr bool DIRECT = std::is_same<M, double>::value;
     // pre-collision pair sums / differences and moments (the axis pairs
     // (1,2), (3,4), (5,6) start j along +x, +y, +z; the diagonal pairs add
     // to it, so no sum starts from a zero)
@@ -452,7 +460,8 @@ __device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams&
     const M orho = om * rho;
     const M base = om * fmad(rho, -uu15, drho);
     const M a1 = M(4.5) * wa * orho, b1 = wa * base;
-    const M a2 = M(4.5) * wb * orho, b2 = wb * base, c2 = M(3) * wb * (omm * rho);
+    const M omr = omm * rho;
+    const M a2 = M(4.5) * wb * orho, b2 = wb * base, c2 = M(3) * wb * omr;
     M fa1 = 0, fb1 = 0, fa2 = 0, fb2 = 0, fc2 = 0;
     if (FORCE) {
         fa1 = M(9) * pref * wa;
@@ -483,7 +492,8 @@ __device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams&
         term(D3Q19::cy(i), uy, Fy);
         term(D3Q19::cz(i), uz, Fz);
     };
-    // the even half-sums of the axis pairs (needed for the mass below)
+    // the even half-sums of the axis pairs (FP32: needed for the mass below;
+    // FP64: the axis pairs are final here)
     M hsa[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -492,8 +502,16 @@ __device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams&
         M even = fmad(a1, cu * cu, b1);
         if (FORCE) even = even + fmad(fa1, cu * cF, fb1);
         hsa[k] = fmad(omh, ps[k], even);
+        if constexpr (DIRECT) {
+            M odd = (M(3) * wa) * omr * cu;
+            if (FORCE) odd = fmad(M(3) * pref_m * wa, cF, odd);
+            const M hd = fmad(omh_m, pd[k], odd);
+            emit(2 * k + 1, hsa[k] + hd);
+            emit(2 * k + 2, hsa[k] - hd);
+        }
     }
-    M msum = hsa[0] + hsa[1] + hsa[2];
+    M msum = 0;
+    if constexpr (!DIRECT) msum = hsa[0] + hsa[1] + hsa[2];
     // half the momentum carried by the 12 diagonal directions; each sum
     // starts at its first term (the flags fold away once the loop is unrolled)
     M ox = 0, oy = 0, oz = 0;
@@ -516,24 +534,33 @@ __device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams&
         M odd = c2 * cu;
         if (FORCE) odd = fmad(fc2, cF, odd);
         const M hd = fmad(omh_m, pd[k], odd);
-        acc(ox, fx, D3Q19::cx(i), hd);
-        acc(oy, fy, D3Q19::cy(i), hd);
-        acc(oz, fz, D3Q19::cz(i), hd);
-        msum += hs;
+        if constexpr (!DIRECT) {
+            acc(ox, fx, D3Q19::cx(i), hd);
+            acc(oy, fy, D3Q19::cy(i), hd);
+            acc(oz, fz, D3Q19::cz(i), hd);
+            msum += hs;
+        }
         emit(i, hs + hd);
         emit(i + 1, hs - hd);
     }
-    // axis pairs (1,2) x, (3,4) y, (5,6) z: post-collision momentum j + F
-    const M hdx = fmad(M(0.5), FORCE ? jx + Fx : jx, -ox);
-    const M hdy = fmad(M(0.5), FORCE ? jy + Fy : jy, -oy);
-    const M hdz = fmad(M(0.5), FORCE ? jz + Fz : jz, -oz);
-    emit(1, hsa[0] + hdx);
-    emit(2, hsa[0] - hdx);
-    emit(3, hsa[1] + hdy);
-    emit(4, hsa[1] - hdy);
-    emit(5, hsa[2] + hdz);
-    emit(6, hsa[2] - hdz);
-    emit(0, fmad(M(-2), msum, drho));  // mass unchanged by the collision
+    if constexpr (DIRECT) {
+        // rest population: (1 - omega) d_0 + omega deq_0 + S_0, c_0 = 0
+        M e0 = M(D3Q19::w(0)) * base;
+        if (FORCE) e0 = fmad(M(-3) * D3Q19::w(0) * pref, uF, e0);
+        emit(0, fmad(M(p.om1), d[0], e0));
+    } else {
+        // axis pairs (1,2) x, (3,4) y, (5,6) z: post-collision momentum j + F
+        const M hdx = fmad(M(0.5), FORCE ? jx + Fx : jx, -ox);
+        const M hdy = fmad(M(0.5), FORCE ? jy + Fy : jy, -oy);
+        const M hdz = fmad(M(0.5), FORCE ? jz + Fz : jz, -oz);
+        emit(1, hsa[0] + hdx);
+        emit(2, hsa[0] - hdx);
+        emit(3, hsa[1] + hdy);
+        emit(4, hsa[1] - hdy);
+        emit(5, hsa[2] + hdz);
+        emit(6, hsa[2] - hdz);
+        emit(0, fmad(M(-2), msum, drho));  // mass unchanged by the collision
+    }
 }
 
 template <class M, bool FORCE>
