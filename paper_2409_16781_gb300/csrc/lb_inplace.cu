@@ -77,11 +77,19 @@ __global__ void __launch_bounds__(512) step_kernel_inplace(const S* Ar, S* Aw, c
 //     one aligned 2-vector store where c_x = 0, one store per cell where the
 //     x-shift would break the alignment.
 // Solid cells of a pair store nothing (as in the one-cell kernel).
+//
+// ROW (16-bit storage from FORM_SWAPPED, nx a multiple of 64 and at most
+// 1024): one block holds a whole row, nx/2 threads.  The values that cross a
+// warp edge (and the periodic wrap at the row's ends) then pass through
+// shared memory, so that every lane issues one aligned pair store per
+// direction and no lane stores a single value: after the block barrier no
+// thread of the row still has to read, and no other block touches the row's
+// slots.  A row with a solid cell takes the general stores below.
 // ---------------------------------------------------------------------------
-template <class S, bool FORCE, int FORM, bool SR>
-__global__ void __launch_bounds__(128, 8) step_kernel_inplace_pairs(const S* Ar, S* Aw,
-                                                                    const uint8_t* __restrict__ code,
-                                                                    LatticeParams p, int xblocks) {
+template <class S, bool FORCE, int FORM, bool SR, bool ROW = false>
+__global__ void __launch_bounds__(ROW ? 512 : 128, ROW ? 2 : 8)
+    step_kernel_inplace_pairs(const S* Ar, S* Aw, const uint8_t* __restrict__ code, LatticeParams p,
+                              int xblocks) {
     using V = typename Vec2<S>::T;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     const int xb = blockIdx.x % xblocks;
@@ -186,45 +194,88 @@ __global__ void __launch_bounds__(128, 8) step_kernel_inplace_pairs(const S* Ar,
                 if (fb) st_pop<0>(q + 1, b);
             }
         };
+        if constexpr (sizeof(S) == 2) {
+            // each pair's two values rounded into one word (low half: cell
+            // x0), which then travels between lanes as a whole
+            uint32_t w[Q];
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            S* rowt = Aw + (int64_t)i * p.ps + yt[D3Q19::cy(i) + 1] + zt[D3Q19::cz(i) + 1];
-            if (D3Q19::cx(i) == 0) {
-                if (f0 && f1) {
-                    pair_store(rowt + x0, i);
-                } else {
-                    if (f0) st_pop<0>(rowt + x0, R.one(d[i].v.x, key, cell0, i));
-                    if (f1) st_pop<0>(rowt + x0 + 1, R.one(d[i].v.y, key, cell0 + 1, i));
+            for (int i = 0; i < Q; ++i) w[i] = R.two(d[i].v.x, d[i].v.y, key, i);
+            if constexpr (ROW) {
+                // lane 31's words of the c_x = +1 directions and lane 0's of
+                // the c_x = -1 directions, per warp (at most 16 warps)
+                __shared__ uint32_t edge[2][5][16];
+                const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+                int kp = 0, km = 0;
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    if (D3Q19::cx(i) == 1) {
+                        if (lane == 31) edge[0][kp][warp] = w[i];
+                        ++kp;
+                    } else if (D3Q19::cx(i) == -1) {
+                        if (lane == 0) edge[1][km][warp] = w[i];
+                        ++km;
+                    }
                 }
-                continue;
+                if (__syncthreads_and(f0 && f1)) {
+                    const int wprev = warp == 0 ? nwarps - 1 : warp - 1;
+                    const int wnext = warp == nwarps - 1 ? 0 : warp + 1;
+                    kp = km = 0;
+#pragma unroll
+                    for (int i = 0; i < Q; ++i) {
+                        uint32_t* q = reinterpret_cast<uint32_t*>(Aw + (int64_t)i * p.ps + yt[D3Q19::cy(i) + 1] +
+                                                                  zt[D3Q19::cz(i) + 1] + x0);
+                        uint32_t v = w[i];
+                        if (D3Q19::cx(i) == 1) {  // slots (x0, x0 + 1) <- (x0 - 1, x0)
+                            uint32_t pw = __shfl_up_sync(0xffffffffu, w[i], 1);
+                            if (lane == 0) pw = edge[0][kp][wprev];
+                            ++kp;
+                            v = __byte_perm(pw, w[i], 0x5432);
+                        } else if (D3Q19::cx(i) == -1) {  // slots (x0, x0 + 1) <- (x0 + 1, x0 + 2)
+                            uint32_t nw = __shfl_down_sync(0xffffffffu, w[i], 1);
+                            if (lane == 31) nw = edge[1][km][wnext];
+                            ++km;
+                            v = __byte_perm(w[i], nw, 0x5432);
+                        }
+                        st_pop<0>(q, v);
+                    }
+                    return;
+                }
             }
-            if constexpr (sizeof(S) == 2) {
-                // both values rounded into one word (low half: cell x0), which
-                // then travels between lanes as a whole
-                const uint32_t w = R.two(d[i].v.x, d[i].v.y, key, i);
-                const S v0 = from_bits16<S>(w & 0xffffu), v1 = from_bits16<S>(w >> 16);
-                if (D3Q19::cx(i) == 1) {  // x0 -> x0 + 1, x0 + 1 -> x0 + 2
-                    const uint32_t pw = __shfl_up_sync(0xffffffffu, w, 1);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                S* rowt = Aw + (int64_t)i * p.ps + yt[D3Q19::cy(i) + 1] + zt[D3Q19::cz(i) + 1];
+                const uint32_t wi = w[i];
+                const S v0 = from_bits16<S>(wi & 0xffffu), v1 = from_bits16<S>(wi >> 16);
+                if (D3Q19::cx(i) == 0) {
+                    put(rowt + x0, v0, v1, f0, f1);
+                } else if (D3Q19::cx(i) == 1) {  // x0 -> x0 + 1, x0 + 1 -> x0 + 2
+                    const uint32_t pw = __shfl_up_sync(0xffffffffu, wi, 1);
                     if (has_prev) {  // slots (x0, x0 + 1) <- (previous lane's x0 - 1, x0)
-                        if (p1 && f0) st_pop<0>(reinterpret_cast<uint32_t*>(rowt + x0), __byte_perm(pw, w, 0x5432));
+                        if (p1 && f0) st_pop<0>(reinterpret_cast<uint32_t*>(rowt + x0), __byte_perm(pw, wi, 0x5432));
                         else put(rowt + x0, from_bits16<S>(pw >> 16), v0, p1, f0);
                     } else if (f0) {
                         st_pop<0>(rowt + x0 + 1, v0);
                     }
                     if (!has_next && f1) st_pop<0>(rowt + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2), v1);
                 } else {  // x0 -> x0 - 1, x0 + 1 -> x0
-                    const uint32_t nw = __shfl_down_sync(0xffffffffu, w, 1);
+                    const uint32_t nw = __shfl_down_sync(0xffffffffu, wi, 1);
                     if (has_next) {  // slots (x0, x0 + 1) <- (x0 + 1, next lane's x0 + 2)
-                        if (f1 && n0) st_pop<0>(reinterpret_cast<uint32_t*>(rowt + x0), __byte_perm(w, nw, 0x5432));
+                        if (f1 && n0) st_pop<0>(reinterpret_cast<uint32_t*>(rowt + x0), __byte_perm(wi, nw, 0x5432));
                         else put(rowt + x0, v1, from_bits16<S>(nw & 0xffffu), f1, n0);
                     } else if (f1) {
                         st_pop<0>(rowt + x0, v1);
                     }
                     if (!has_prev && f0) st_pop<0>(rowt + (x0 == 0 ? nx - 1 : x0 - 1), v0);
                 }
-            } else {
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                S* rowt = Aw + (int64_t)i * p.ps + yt[D3Q19::cy(i) + 1] + zt[D3Q19::cz(i) + 1];
                 const S v0 = R.one(d[i].v.x, key, cell0, i), v1 = R.one(d[i].v.y, key, cell0 + 1, i);
-                if (D3Q19::cx(i) == 1) {  // x0 -> x0 + 1, x0 + 1 -> x0 + 2
+                if (D3Q19::cx(i) == 0) {
+                    put(rowt + x0, v0, v1, f0, f1);
+                } else if (D3Q19::cx(i) == 1) {  // x0 -> x0 + 1, x0 + 1 -> x0 + 2
                     const S pv = shfl_val<S>(v1, true);  // the previous lane's x0 - 1 -> x0
                     if (has_prev) put(rowt + x0, pv, v0, p1, f0);
                     else if (f0) st_pop<0>(rowt + x0 + 1, v0);
@@ -243,6 +294,19 @@ __global__ void __launch_bounds__(128, 8) step_kernel_inplace_pairs(const S* Ar,
 template <class S, int FORM, bool SR>
 static cudaError_t step_inplace_pairs_form(void* A, const uint8_t* code, const LatticeParams& p, int block,
                                            cudaStream_t st) {
+    const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
+    if constexpr (sizeof(S) == 2 && FORM == FORM_SWAPPED) {
+        if (p.nx % 64 == 0 && p.nx <= 1024) {  // one block per row, nx/2 threads
+            const unsigned rows = (unsigned)((int64_t)p.ny * p.nz);
+            if (force)
+                step_kernel_inplace_pairs<S, true, FORM, SR, true>
+                    <<<rows, p.nx / 2, 0, st>>>((const S*)A, (S*)A, code, p, 1);
+            else
+                step_kernel_inplace_pairs<S, false, FORM, SR, true>
+                    <<<rows, p.nx / 2, 0, st>>>((const S*)A, (S*)A, code, p, 1);
+            return cudaGetLastError();
+        }
+    }
     int bx = block > 0 ? (block / 32) * 32 : 64;  // whole warps (the shuffles need all 32 lanes)
     if (bx < 32) bx = 32;
     if (bx > 128) bx = 128;
@@ -251,7 +315,6 @@ static cudaError_t step_inplace_pairs_form(void* A, const uint8_t* code, const L
     if (bx > need) bx = need;
     const int xblocks = (pairs + bx - 1) / bx;
     const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
-    const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if (force)
         step_kernel_inplace_pairs<S, true, FORM, SR>
             <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);

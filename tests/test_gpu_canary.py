@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 GUARD = 1 << 16      # bytes before and after; a multiple of the 256-byte alignment
 PATTERN = 0xA5
-SHAPES = ((34, 7, 6), (35, 6, 5), (48, 5, 4), (1, 1, 1), (66, 3, 2))
+SHAPES = ((34, 7, 6), (35, 6, 5), (48, 5, 4), (1, 1, 1), (66, 3, 2), (64, 4, 3), (128, 3, 2))
 
 
 def _flags(nx, ny, nz, seed):

@@ -19,7 +19,7 @@ from paper_2409_16781_gb300.lattice import make_options
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = ((34, 7, 6), (35, 6, 5), (48, 5, 4), (1, 1, 1), (2, 3, 1), (66, 3, 2))
+SHAPES = ((34, 7, 6), (35, 6, 5), (48, 5, 4), (1, 1, 1), (2, 3, 1), (66, 3, 2), (64, 4, 3), (128, 3, 2))
 STEPS = 3
 
 

@@ -48,6 +48,14 @@ CASES = [
     (33, 5, 3, 0.55, None, (0, 0, 0), (2e-5, 1e-5, 0)),
     (70, 3, 2, 0.9, ("cavity", 0), (0.1, 0, 0), (0, 0, 0)),
     (66, 5, 4, 0.7, ("random", 22), (0.02, 0.0, 0.0), (5e-5, 0, 1e-4)),
+    # nx a multiple of 64 up to 1024: 16-bit rows from the swapped layout in
+    # one block each -- all-fluid rows (aligned stores only), rows with walls
+    # (the general stores), a mix, and the largest block (16 warps)
+    (128, 4, 3, 0.6, None, (0, 0, 0), (1e-5, 2e-5, 0)),
+    (64, 6, 5, 0.7, ("random", 5), (0.04, 0.0, 0.01), (3e-5, 0, -2e-5)),
+    (64, 7, 6, 0.75, ("sparse", 8), (0.03, 0.0, 0.0), (0, 0, 0)),
+    (1024, 2, 3, 0.65, None, (0, 0, 0), (0, 1e-5, 0)),
+    (192, 3, 4, 0.65, ("sparse", 3), (0.02, 0.01, 0.0), (0, 0, 0)),
 ]
 
 
@@ -57,6 +65,8 @@ def _flags(spec, nx, ny, nz):
     kind, seed = spec
     if kind == "random":
         return W.random_flags(nx, ny, nz, seed=seed, p_wall=0.2, p_lid=0.1)
+    if kind == "sparse":  # about half the 64-cell rows without a wall
+        return W.random_flags(nx, ny, nz, seed=seed, p_wall=0.01, p_lid=0.005)
     return W.cavity_flags(nx, ny, nz)
 
 
