@@ -116,20 +116,31 @@ __global__ void __launch_bounds__(ROW ? 512 : 128, ROW ? 2 : 8)
         const int zo[3] = {(z == nz - 1 ? 0 : z + 1) * nxy, z * nxy, (z == 0 ? nz - 1 : z - 1) * nxy};
         const bool own_prev = lane == 0 || x0 == 0;
         const bool own_next = lane == 31 || x0 + 2 >= nx;
+        // every load first, then the unpacking and the shuffles (as in the
+        // two-array pair kernel)
+        const int xprev = x0 == 0 ? nx - 1 : x0 - 1, xnext = x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2;
+        V v[Q];
+        S e[Q];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const S* rowp = Ar + (int64_t)D3Q19::opp(i) * p.ps + yo[D3Q19::cy(i) + 1] + zo[D3Q19::cz(i) + 1];
+            v[i] = ld_pop<0>(reinterpret_cast<const V*>(rowp + x0));
+            if (D3Q19::cx(i) == 1 && own_prev && active) e[i] = ld_pop<0>(rowp + xprev);
+            if (D3Q19::cx(i) == -1 && own_next && active) e[i] = ld_pop<0>(rowp + xnext);
+        }
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
             float a, b;
-            split2<S>(ld_pop<0>(reinterpret_cast<const V*>(rowp + x0)), a, b);
+            split2<S>(v[i], a, b);
             if (D3Q19::cx(i) == 0) {
                 d[i] = f32x2(a, b);
             } else if (D3Q19::cx(i) == 1) {  // source x - 1
                 float prev = __shfl_up_sync(0xffffffffu, b, 1);
-                if (own_prev && active) prev = Storage<S>::load(ld_pop<0>(rowp + (x0 == 0 ? nx - 1 : x0 - 1)));
+                if (own_prev && active) prev = Storage<S>::load(e[i]);
                 d[i] = f32x2(prev, a);
             } else {  // source x + 1
                 float next = __shfl_down_sync(0xffffffffu, a, 1);
-                if (own_next && active) next = Storage<S>::load(ld_pop<0>(rowp + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2)));
+                if (own_next && active) next = Storage<S>::load(e[i]);
                 d[i] = f32x2(b, next);
             }
         }
