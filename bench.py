@@ -39,6 +39,8 @@ import sys
 import threading
 import time
 
+T_START = time.time()  # process start: the configs sections stop starting after --configs-deadline-s
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -106,6 +108,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the porous 512^3, cavity 768^3 precision and 2000-request serving sections")
     ap.add_argument("--precision-steps", type=int, default=5000, help="steps of the 768^3 precision study")
+    ap.add_argument("--configs-deadline-s", type=float, default=2400.0,
+                    help="a configs section that would start later than this many seconds after the "
+                         "process started is skipped (reported as skipped), so the line is always printed")
     return ap.parse_args(argv)
 
 
@@ -856,6 +861,10 @@ def configs_section(args):
     )
     for name, fn in sections:
         t1 = time.time()
+        if t1 - T_START > args.configs_deadline_s:
+            out[name] = {"skipped": f"started {t1 - T_START:.0f} s after the process, past the "
+                                    f"{args.configs_deadline_s:.0f} s deadline"}
+            continue
         try:
             out[name] = fn()
         except Exception as e:  # a failed section is reported, the line still printed

@@ -98,7 +98,7 @@ typedef struct lb_options {
                           batch slot gives bitwise the same result, and a
                           checkpoint restores the stream with the step
                           count.  Supported by step variants 1-3, 13, 15,
-                          16, 17 and the in-place kernels; other variants
+                          16, 17, 18 and the in-place kernels; other variants
                           run 15 (1 where it does not apply).  Equilibrium
                           initialisation and population import round to
                           nearest even. */
@@ -226,7 +226,8 @@ int lb_get_populations_at(lb_lattice *h, const int64_t *cells, int n, double *ou
 
 /* Step-kernel choice.  Variants: 0 library default (measured on GB300:
  * FP32 and Mixed2 one cell per thread, FP64 two cells per thread, 16-bit
- * storage variant 15); 1 one cell per thread;
+ * storage variant 18, or 15 where the row does not fit it); 1 one cell per
+ * thread;
  * 2, 3 as 1 with streaming / L2-only cache policies; 4, 5 two cells per
  * thread (even nx); 6, 7 two cells per thread, packed 16-bit registers
  * (16-bit storage, even nx); 8, 9 four cells per thread, packed 16-bit
@@ -239,7 +240,10 @@ int lb_get_populations_at(lb_lattice *h, const int64_t *cells, int n, double *ou
  * 16 as 1 and 17 as 15, each with the bounce-back of cells next to a wall
  * reordered (all neighbour flags read first, then every value load issued
  * together): same results, faster on lattices with many wall cells (porous
- * media), a little slower elsewhere; 16 caps blocks at 128 threads.
+ * media), a little slower elsewhere; 16 caps blocks at 128 threads;
+ * 18 as 15 with one block per row, the values crossing a warp edge passed
+ * through shared memory (nx % 64 == 0 and nx <= 1024, else 15; block size
+ * fixed at nx / 2).
  * A variant that does not apply to the lattice runs
  * variant 1.  In-place lattices have their own two kernels (see
  * lb_options.inplace: variant 2 two cells per thread, others one).

@@ -53,12 +53,11 @@ __device__ __forceinline__ typename Vec2<S>::T pack_vals(S a, S b) {
 template <class S, bool FORCE, int FORM, bool SR>
 __global__ void __launch_bounds__(512) step_kernel_inplace(const S* Ar, S* Aw, const uint8_t* __restrict__ code,
                                                            LatticeParams p, int xblocks) {
-    const int xb = blockIdx.x % xblocks;
-    const int row = blockIdx.x / xblocks;
+    int xb, y, z;
+    block_row(xblocks, p.ny, xb, y, z);
+    const int row = y + p.ny * z;
     const int x = xb * blockDim.x + threadIdx.x;
     if (x >= p.nx) return;
-    const int y = row % p.ny;
-    const int z = row / p.ny;
     const int cell = x + p.nx * row;
     const uint8_t cc = code[cell];
     if (cc & CODE_TYPE) return;  // solid cells hold no values of their own
@@ -92,10 +91,9 @@ __global__ void __launch_bounds__(ROW ? 512 : 128, ROW ? 2 : 8)
                               int xblocks) {
     using V = typename Vec2<S>::T;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int xb = blockIdx.x % xblocks;
-    const int row = blockIdx.x / xblocks;
-    const int y = row % ny;
-    const int z = row / ny;
+    int xb, y, z;
+    block_row(xblocks, ny, xb, y, z);
+    const int row = y + ny * z;
     const int x0r = 2 * (xb * blockDim.x + threadIdx.x);
     const bool active = x0r < nx;
     const int x0 = active ? x0r : 0;  // in-bounds address for idle lanes
@@ -125,9 +123,51 @@ __global__ void __launch_bounds__(ROW ? 512 : 128, ROW ? 2 : 8)
         for (int i = 0; i < Q; ++i) {
             const S* rowp = Ar + (int64_t)D3Q19::opp(i) * p.ps + yo[D3Q19::cy(i) + 1] + zo[D3Q19::cz(i) + 1];
             v[i] = ld_pop<0>(reinterpret_cast<const V*>(rowp + x0));
-            if (D3Q19::cx(i) == 1 && own_prev && active) e[i] = ld_pop<0>(rowp + xprev);
-            if (D3Q19::cx(i) == -1 && own_next && active) e[i] = ld_pop<0>(rowp + xnext);
+            if constexpr (!ROW) {
+                if (D3Q19::cx(i) == 1 && own_prev && active) e[i] = ld_pop<0>(rowp + xprev);
+                if (D3Q19::cx(i) == -1 && own_next && active) e[i] = ld_pop<0>(rowp + xnext);
+            }
         }
+        if constexpr (ROW) {
+            // whole-row block: the values that cross a warp edge (and the
+            // periodic wrap) come from the neighbouring warp through shared
+            // memory -- lane 31's second cell for c_x = +1, lane 0's first
+            // cell for c_x = -1 -- instead of a second load by the edge lane
+            __shared__ float edge_in[2][5][16];
+            const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+            int kp = 0, km = 0;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                float a, b;
+                split2<S>(v[i], a, b);
+                d[i] = f32x2(a, b);
+                if (D3Q19::cx(i) == 1) {
+                    if (lane == 31) edge_in[0][kp][warp] = b;
+                    ++kp;
+                } else if (D3Q19::cx(i) == -1) {
+                    if (lane == 0) edge_in[1][km][warp] = a;
+                    ++km;
+                }
+            }
+            __syncthreads();
+            const int wprev = warp == 0 ? nwarps - 1 : warp - 1;
+            const int wnext = warp == nwarps - 1 ? 0 : warp + 1;
+            kp = km = 0;
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                if (D3Q19::cx(i) == 1) {  // source x - 1
+                    float prev = __shfl_up_sync(0xffffffffu, d[i].v.y, 1);
+                    if (lane == 0) prev = edge_in[0][kp][wprev];
+                    ++kp;
+                    d[i] = f32x2(prev, d[i].v.x);
+                } else if (D3Q19::cx(i) == -1) {  // source x + 1
+                    float next = __shfl_down_sync(0xffffffffu, d[i].v.x, 1);
+                    if (lane == 31) next = edge_in[1][km][wnext];
+                    ++km;
+                    d[i] = f32x2(d[i].v.y, next);
+                }
+            }
+        } else {
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             float a, b;
@@ -143,6 +183,7 @@ __global__ void __launch_bounds__(ROW ? 512 : 128, ROW ? 2 : 8)
                 if (own_next && active) next = Storage<S>::load(e[i]);
                 d[i] = f32x2(b, next);
             }
+        }
         }
     }
     const uint8_t c0 = code[cell0], c1 = code[cell0 + 1];
@@ -308,13 +349,12 @@ static cudaError_t step_inplace_pairs_form(void* A, const uint8_t* code, const L
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if constexpr (sizeof(S) == 2 && FORM == FORM_SWAPPED) {
         if (p.nx % 64 == 0 && p.nx <= 1024) {  // one block per row, nx/2 threads
-            const unsigned rows = (unsigned)((int64_t)p.ny * p.nz);
             if (force)
                 step_kernel_inplace_pairs<S, true, FORM, SR, true>
-                    <<<rows, p.nx / 2, 0, st>>>((const S*)A, (S*)A, code, p, 1);
+                    <<<row_grid(1, p.ny, p.nz), p.nx / 2, 0, st>>>((const S*)A, (S*)A, code, p, 1);
             else
                 step_kernel_inplace_pairs<S, false, FORM, SR, true>
-                    <<<rows, p.nx / 2, 0, st>>>((const S*)A, (S*)A, code, p, 1);
+                    <<<row_grid(1, p.ny, p.nz), p.nx / 2, 0, st>>>((const S*)A, (S*)A, code, p, 1);
             return cudaGetLastError();
         }
     }
@@ -325,13 +365,12 @@ static cudaError_t step_inplace_pairs_form(void* A, const uint8_t* code, const L
     const int need = ((pairs + 31) / 32) * 32;
     if (bx > need) bx = need;
     const int xblocks = (pairs + bx - 1) / bx;
-    const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
     if (force)
         step_kernel_inplace_pairs<S, true, FORM, SR>
-            <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);
+            <<<row_grid(xblocks, p.ny, p.nz), bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);
     else
         step_kernel_inplace_pairs<S, false, FORM, SR>
-            <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);
+            <<<row_grid(xblocks, p.ny, p.nz), bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);
     return cudaGetLastError();
 }
 
@@ -344,12 +383,11 @@ static cudaError_t step_inplace_form(void* A, const uint8_t* code, const Lattice
     const int need = ((p.nx + 31) / 32) * 32;  // shrink the block for narrow rows
     if (bx > need) bx = need;
     const int xblocks = (p.nx + bx - 1) / bx;
-    const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if (force)
-        step_kernel_inplace<S, true, FORM, SR><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);
+        step_kernel_inplace<S, true, FORM, SR><<<row_grid(xblocks, p.ny, p.nz), bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);
     else
-        step_kernel_inplace<S, false, FORM, SR><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);
+        step_kernel_inplace<S, false, FORM, SR><<<row_grid(xblocks, p.ny, p.nz), bx, 0, st>>>((const S*)A, (S*)A, code, p, xblocks);
     return cudaGetLastError();
 }
 

@@ -33,6 +33,29 @@ static __device__ unsigned long long g_violations;
 static __device__ unsigned long long g_checks;  // accesses checked (shows the checks ran)
 #endif
 
+// Row-mapped launches: `xblocks` blocks along x for every row (y, z).  The
+// grid is three-dimensional (blockIdx.y = y, blockIdx.z = z) whenever ny and
+// nz fit its y and z limits, which spares every block the two integer
+// divisions of a flat row index; otherwise it is one flat x dimension of
+// xblocks * ny * nz blocks.  gridDim.x tells the kernel which: it equals
+// xblocks only for the 3D grid (or for a single row, where both agree).
+inline dim3 row_grid(int xblocks, int ny, int nz) {
+    if (ny <= 65535 && nz <= 65535) return dim3((unsigned)xblocks, (unsigned)ny, (unsigned)nz);
+    return dim3((unsigned)((int64_t)xblocks * ny * nz), 1u, 1u);
+}
+__device__ __forceinline__ void block_row(int xblocks, int ny, int& xb, int& y, int& z) {
+    if (gridDim.x == (unsigned)xblocks) {
+        xb = (int)blockIdx.x;
+        y = (int)blockIdx.y;
+        z = (int)blockIdx.z;
+    } else {
+        const int row = (int)blockIdx.x / xblocks;
+        xb = (int)blockIdx.x - row * xblocks;
+        y = row % ny;
+        z = row / ny;
+    }
+}
+
 // Global loads/stores of population values with a cache policy:
 //   HINT 0: default (L1 + L2),  1: streaming (.cs, evict-first),
 //   HINT 2: L2 only for loads (.cg), streaming stores.
@@ -311,7 +334,18 @@ __device__ __forceinline__ f32x2 operator+(f32x2 a, f32x2 b) {
     return r;
 }
 __device__ __forceinline__ f32x2 operator-(f32x2 a) { return f32x2(-a.v.x, -a.v.y); }
-__device__ __forceinline__ f32x2 operator-(f32x2 a, f32x2 b) { return a + (-b); }
+// a - b as one packed subtraction (each lane rounded as the scalar
+// subtraction), not as an addition of a separately negated pair
+__device__ __forceinline__ f32x2 operator-(f32x2 a, f32x2 b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;"
+        : "=l"(r)
+        : "l"(*reinterpret_cast<const unsigned long long*>(&a.v)),
+          "l"(*reinterpret_cast<const unsigned long long*>(&b.v)));
+    f32x2 o;
+    o.v = *reinterpret_cast<const float2*>(&r);
+    return o;
+}
 __device__ __forceinline__ f32x2 operator*(f32x2 a, f32x2 b) {
     f32x2 r;
     r.v = __fmul2_rn(a.v, b.v);
@@ -439,7 +473,9 @@ __device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams&
     }
     const M om = param<M>(p.omega, p.omega_f);
     const M omm = param<M>(p.omega_m, p.omega_m_f);
-    const M uu15 = M(1.5) * fmad(ux, ux, fmad(uy, uy, uz * uz));
+    // -1.5 u.u (rounding is symmetric in sign, so this is exactly -(1.5 u.u),
+    // and no operand below needs a negation)
+    const M nuu15 = M(-1.5) * fmad(ux, ux, fmad(uy, uy, uz * uz));
     M Fx = 0, Fy = 0, Fz = 0, uF = 0, pref = 0, pref_m = 0;
     if (FORCE) {
         Fx = rho * param<M>(p.g[0], p.g_f[0]);
@@ -458,7 +494,7 @@ __device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams&
     const M omh = param<M>(p.omh, p.omh_f);
     const M omh_m = param<M>(p.omh_m, p.omh_m_f);
     const M orho = om * rho;
-    const M base = om * fmad(rho, -uu15, drho);
+    const M base = om * fmad(rho, nuu15, drho);
     const M a1 = M(4.5) * wa * orho, b1 = wa * base;
     const M omr = omm * rho;
     const M a2 = M(4.5) * wb * orho, b2 = wb * base, c2 = M(3) * wb * omr;
@@ -549,16 +585,18 @@ __device__ __forceinline__ void relax_emit(const M (&d)[Q], const LatticeParams&
         if (FORCE) e0 = fmad(M(-3) * D3Q19::w(0) * pref, uF, e0);
         emit(0, fmad(M(p.om1), d[0], e0));
     } else {
-        // axis pairs (1,2) x, (3,4) y, (5,6) z: post-collision momentum j + F
-        const M hdx = fmad(M(0.5), FORCE ? jx + Fx : jx, -ox);
-        const M hdy = fmad(M(0.5), FORCE ? jy + Fy : jy, -oy);
-        const M hdz = fmad(M(0.5), FORCE ? jz + Fz : jz, -oz);
-        emit(1, hsa[0] + hdx);
-        emit(2, hsa[0] - hdx);
-        emit(3, hsa[1] + hdy);
-        emit(4, hsa[1] - hdy);
-        emit(5, hsa[2] + hdz);
-        emit(6, hsa[2] - hdz);
+        // axis pairs (1,2) x, (3,4) y, (5,6) z: post-collision momentum j + F;
+        // nhd = o - (j [+ F]) / 2 is exactly minus the half difference
+        // (j [+ F]) / 2 - o, so the pair is (hs - nhd, hs + nhd)
+        const M nhdx = fmad(M(-0.5), FORCE ? jx + Fx : jx, ox);
+        const M nhdy = fmad(M(-0.5), FORCE ? jy + Fy : jy, oy);
+        const M nhdz = fmad(M(-0.5), FORCE ? jz + Fz : jz, oz);
+        emit(1, hsa[0] - nhdx);
+        emit(2, hsa[0] + nhdx);
+        emit(3, hsa[1] - nhdy);
+        emit(4, hsa[1] + nhdy);
+        emit(5, hsa[2] - nhdz);
+        emit(6, hsa[2] + nhdz);
         emit(0, fmad(M(-2), msum, drho));  // mass unchanged by the collision
     }
 }

@@ -96,7 +96,12 @@ __device__ __forceinline__ void bounce_fix_x2(const S* __restrict__ A, const uin
 // comes from the previous lane's second cell and the value at x0+2 (c_x =
 // -1) from the next lane's first cell when that lane holds the same row;
 // otherwise (warp edge, row edge, periodic wrap) the lane loads it itself.
-template <class S, bool FORCE, int HINT, bool MASK_FIRST = false, bool SR = false>
+//
+// ROW: the block is the whole row (nx / 2 threads, nx a multiple of 64 and at
+// most 1024, every lane active).  The values that cross a warp edge, and the
+// periodic wrap at the row's ends, then pass through shared memory after one
+// block barrier instead of being loaded again by the edge lanes.
+template <class S, bool FORCE, int HINT, bool MASK_FIRST = false, bool SR = false, bool ROW = false>
 __device__ __forceinline__ void pair_x2_update(const S* __restrict__ A, S* __restrict__ B,
                                                const uint8_t* __restrict__ code, const LatticeParams& p, int x0,
                                                int y, int z, int cell0, int lane, bool active) {
@@ -108,6 +113,50 @@ __device__ __forceinline__ void pair_x2_update(const S* __restrict__ A, S* __res
     const bool own_prev = lane == 0 || x0 == 0;        // x0-1 not in the previous lane
     const bool own_next = lane == 31 || x0 + 2 >= nx;  // x0+2 not in the next lane
     f32x2 d[Q];
+    if constexpr (ROW) {
+        // every pair load first; then lane 31 of each warp publishes its
+        // second cell's values of the c_x = +1 directions and lane 0 its
+        // first cell's values of the c_x = -1 directions (at most 16 warps)
+        __shared__ float edge[2][5][16];
+        const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        V v[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            v[i] = ld_pop<HINT>(reinterpret_cast<const V*>(A + (int64_t)i * p.ps + yo[D3Q19::cy(i) + 1] +
+                                                           zo[D3Q19::cz(i) + 1] + x0));
+        int kp = 0, km = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            float a, b;
+            split2<S>(v[i], a, b);
+            d[i] = f32x2(a, b);
+            if (D3Q19::cx(i) == 1) {
+                if (lane == 31) edge[0][kp][warp] = b;
+                ++kp;
+            } else if (D3Q19::cx(i) == -1) {
+                if (lane == 0) edge[1][km][warp] = a;
+                ++km;
+            }
+        }
+        __syncthreads();
+        const int wprev = warp == 0 ? nwarps - 1 : warp - 1;
+        const int wnext = warp == nwarps - 1 ? 0 : warp + 1;
+        kp = km = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            if (D3Q19::cx(i) == 1) {  // (x0 - 1, x0) <- (previous lane's x0 - 1, own x0)
+                float prev = __shfl_up_sync(0xffffffffu, d[i].v.y, 1);
+                if (lane == 0) prev = edge[0][kp][wprev];
+                ++kp;
+                d[i] = f32x2(prev, d[i].v.x);
+            } else if (D3Q19::cx(i) == -1) {  // (x0 + 1, x0 + 2) <- (own x0 + 1, next lane's x0 + 2)
+                float next = __shfl_down_sync(0xffffffffu, d[i].v.x, 1);
+                if (lane == 31) next = edge[1][km][wnext];
+                ++km;
+                d[i] = f32x2(d[i].v.y, next);
+            }
+        }
+    } else {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const S* rowp = A + (int64_t)i * p.ps + yo[D3Q19::cy(i) + 1] + zo[D3Q19::cz(i) + 1];
@@ -126,6 +175,7 @@ __device__ __forceinline__ void pair_x2_update(const S* __restrict__ A, S* __res
                 next = Storage<S>::load(ld_pop<HINT>(rowp + (x0 + 2 >= nx ? x0 + 2 - nx : x0 + 2)));
             d[i] = f32x2(b, next);
         }
+    }
     }
     if (!active) return;
     const uint8_t c0 = code[cell0], c1 = code[cell0 + 1];

@@ -34,12 +34,11 @@ __global__ void __launch_bounds__(MASK_FIRST ? 128 : 512, MASK_FIRST ? 10 : 0)
     step_kernel_rows(const S* __restrict__ A, S* __restrict__ B, const uint8_t* __restrict__ code, LatticeParams p,
                      int xblocks) {
     using M = typename Storage<S>::math;
-    const int xb = blockIdx.x % xblocks;
-    const int row = blockIdx.x / xblocks;
+    int xb, y, z;
+    block_row(xblocks, p.ny, xb, y, z);
+    const int row = y + p.ny * z;
     const int x = xb * blockDim.x + threadIdx.x;
     if (x >= p.nx) return;
-    const int y = row % p.ny;
-    const int z = row / p.ny;
     const int cell = x + p.nx * row;
     const uint8_t cc = code[cell];
     if (cc & CODE_TYPE) return;  // solid cells are never written
@@ -68,10 +67,9 @@ __global__ void __launch_bounds__(256) step_kernel_pairs(const S* __restrict__ A
     using M = typename Storage<S>::math;
     using V = typename Vec2<S>::T;
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int xb = blockIdx.x % xblocks;
-    const int row = blockIdx.x / xblocks;
-    const int y = row % ny;
-    const int z = row / ny;
+    int xb, y, z;
+    block_row(xblocks, ny, xb, y, z);
+    const int row = y + ny * z;
     const int x0 = 2 * (xb * blockDim.x + threadIdx.x);
     const bool active = x0 < nx;
     const int xa = active ? x0 : 0;  // in-bounds address for idle lanes
@@ -137,12 +135,11 @@ static cudaError_t step_pairs_t(const void* A, void* B, const uint8_t* code, con
     const int need = ((pairs + 31) / 32) * 32;
     if (bx > need) bx = need;
     const int xblocks = (pairs + bx - 1) / bx;
-    const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if (force)
-        step_kernel_pairs<S, true, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+        step_kernel_pairs<S, true, HINT><<<row_grid(xblocks, p.ny, p.nz), bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     else
-        step_kernel_pairs<S, false, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+        step_kernel_pairs<S, false, HINT><<<row_grid(xblocks, p.ny, p.nz), bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     return cudaGetLastError();
 }
 
@@ -183,10 +180,9 @@ __global__ void __launch_bounds__(256, 3) step_kernel_pairs16(const S* __restric
     static_assert(sizeof(S) == 2, "16-bit storage only");
     const uint16_t* __restrict__ A16 = reinterpret_cast<const uint16_t*>(A);
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int xb = blockIdx.x % xblocks;
-    const int row = blockIdx.x / xblocks;
-    const int y = row % ny;
-    const int z = row / ny;
+    int xb, y, z;
+    block_row(xblocks, ny, xb, y, z);
+    const int row = y + ny * z;
     const int x0 = 2 * (xb * blockDim.x + threadIdx.x);
     const bool active = x0 < nx;
     const int xa = active ? x0 : 0;  // in-bounds address for idle lanes
@@ -259,12 +255,11 @@ static cudaError_t step_pairs16_t(const void* A, void* B, const uint8_t* code, c
     const int need = ((pairs + 31) / 32) * 32;
     if (bx > need) bx = need;
     const int xblocks = (pairs + bx - 1) / bx;
-    const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if (force)
-        step_kernel_pairs16<S, true, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+        step_kernel_pairs16<S, true, HINT><<<row_grid(xblocks, p.ny, p.nz), bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     else
-        step_kernel_pairs16<S, false, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+        step_kernel_pairs16<S, false, HINT><<<row_grid(xblocks, p.ny, p.nz), bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     return cudaGetLastError();
 }
 
@@ -288,10 +283,9 @@ __global__ void __launch_bounds__(128, 4) step_kernel_quads16(const S* __restric
     static_assert(sizeof(S) == 2, "16-bit storage only");
     const uint16_t* __restrict__ A16 = reinterpret_cast<const uint16_t*>(A);
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int xb = blockIdx.x % xblocks;
-    const int row = blockIdx.x / xblocks;
-    const int y = row % ny;
-    const int z = row / ny;
+    int xb, y, z;
+    block_row(xblocks, ny, xb, y, z);
+    const int row = y + ny * z;
     const int x0 = 4 * (xb * blockDim.x + threadIdx.x);
     const bool active = x0 < nx;
     const int xa = active ? x0 : 0;  // in-bounds address for idle lanes
@@ -367,12 +361,11 @@ static cudaError_t step_quads16_t(const void* A, void* B, const uint8_t* code, c
     const int need = ((quads + 31) / 32) * 32;
     if (bx > need) bx = need;
     const int xblocks = (quads + bx - 1) / bx;
-    const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if (force)
-        step_kernel_quads16<S, true, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+        step_kernel_quads16<S, true, HINT><<<row_grid(xblocks, p.ny, p.nz), bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     else
-        step_kernel_quads16<S, false, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+        step_kernel_quads16<S, false, HINT><<<row_grid(xblocks, p.ny, p.nz), bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     return cudaGetLastError();
 }
 
@@ -393,17 +386,20 @@ static cudaError_t step_quads16_t(const void* A, void* B, const uint8_t* code, c
 // Cells next to a wall leave the packed form for the bounce-back fix-up of
 // each cell and re-enter it.
 // ---------------------------------------------------------------------------
-template <class S, bool FORCE, int HINT, int MINB, bool MASK_FIRST = false, bool SR = false>
-__global__ void __launch_bounds__(256 / MINB, MINB == 1 ? 0 : 4 * MINB)
+//   18: variant 15 with whole-row blocks (nx a multiple of 64, at most 1024;
+//       else variant 15): the values that cross a warp edge come from the
+//       neighbouring warp through shared memory (ROW of pair_x2_update).
+template <class S, bool FORCE, int HINT, int MINB, bool MASK_FIRST = false, bool SR = false, bool ROW = false>
+__global__ void __launch_bounds__(ROW ? 512 : 256 / MINB, ROW ? 2 : (MINB == 1 ? 0 : 4 * MINB))
     step_kernel_pairs_x2(const S* __restrict__ A, S* __restrict__ B, const uint8_t* __restrict__ code, LatticeParams p,
                          int xblocks) {
-    const int xb = blockIdx.x % xblocks;
-    const int row = blockIdx.x / xblocks;
+    int xb, y, z;
+    block_row(xblocks, p.ny, xb, y, z);
     const int x0 = 2 * (xb * blockDim.x + threadIdx.x);
-    const bool active = x0 < p.nx;
+    const bool active = ROW || x0 < p.nx;
     const int xa = active ? x0 : 0;  // in-bounds address for idle lanes
-    pair_x2_update<S, FORCE, HINT, MASK_FIRST, SR>(A, B, code, p, xa, row % p.ny, row / p.ny, xa + p.nx * row,
-                                                   threadIdx.x & 31, active);
+    pair_x2_update<S, FORCE, HINT, MASK_FIRST, SR, ROW>(A, B, code, p, xa, y, z, xa + p.nx * (y + p.ny * z),
+                                                        threadIdx.x & 31, active);
 }
 
 template <class S, int HINT, int MINB, bool MASK_FIRST = false, bool SR = false>
@@ -416,14 +412,29 @@ static cudaError_t step_pairs_x2_t(const void* A, void* B, const uint8_t* code, 
     const int need = ((pairs + 31) / 32) * 32;
     if (bx > need) bx = need;
     const int xblocks = (pairs + bx - 1) / bx;
-    const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if (force)
         step_kernel_pairs_x2<S, true, HINT, MINB, MASK_FIRST, SR>
-            <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+            <<<row_grid(xblocks, p.ny, p.nz), bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     else
         step_kernel_pairs_x2<S, false, HINT, MINB, MASK_FIRST, SR>
-            <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+            <<<row_grid(xblocks, p.ny, p.nz), bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+    return cudaGetLastError();
+}
+
+// Variant 18: one block per row, nx / 2 threads (variant 15 where the row
+// does not fit whole warps or one block).
+template <class S, int HINT, bool SR = false>
+static cudaError_t step_pairs_x2_row_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p,
+                                       cudaStream_t st) {
+    if (p.nx % 64 != 0 || p.nx > 1024) return step_pairs_x2_t<S, HINT, 2, false, SR>(A, B, code, p, 64, st);
+    const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
+    if (force)
+        step_kernel_pairs_x2<S, true, HINT, 2, false, SR, true>
+            <<<row_grid(1, p.ny, p.nz), p.nx / 2, 0, st>>>((const S*)A, (S*)B, code, p, 1);
+    else
+        step_kernel_pairs_x2<S, false, HINT, 2, false, SR, true>
+            <<<row_grid(1, p.ny, p.nz), p.nx / 2, 0, st>>>((const S*)A, (S*)B, code, p, 1);
     return cudaGetLastError();
 }
 
@@ -434,10 +445,9 @@ __global__ void __launch_bounds__(128, 4) step_kernel_quads16_x2(const S* __rest
     static_assert(sizeof(S) == 2, "16-bit storage only");
     const uint16_t* __restrict__ A16 = reinterpret_cast<const uint16_t*>(A);
     const int nx = p.nx, ny = p.ny, nz = p.nz;
-    const int xb = blockIdx.x % xblocks;
-    const int row = blockIdx.x / xblocks;
-    const int y = row % ny;
-    const int z = row / ny;
+    int xb, y, z;
+    block_row(xblocks, ny, xb, y, z);
+    const int row = y + ny * z;
     const int x0 = 4 * (xb * blockDim.x + threadIdx.x);
     const bool active = x0 < nx;
     const int xa = active ? x0 : 0;  // in-bounds address for idle lanes
@@ -505,12 +515,11 @@ static cudaError_t step_quads16_x2_t(const void* A, void* B, const uint8_t* code
     const int need = ((quads + 31) / 32) * 32;
     if (bx > need) bx = need;
     const int xblocks = (quads + bx - 1) / bx;
-    const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if (force)
-        step_kernel_quads16_x2<S, true, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+        step_kernel_quads16_x2<S, true, HINT><<<row_grid(xblocks, p.ny, p.nz), bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     else
-        step_kernel_quads16_x2<S, false, HINT><<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+        step_kernel_quads16_x2<S, false, HINT><<<row_grid(xblocks, p.ny, p.nz), bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     return cudaGetLastError();
 }
 
@@ -843,21 +852,20 @@ static cudaError_t step_rows_t(const void* A, void* B, const uint8_t* code, cons
     const int need = ((p.nx + 31) / 32) * 32;
     if (bx > need) bx = need;
     const int xblocks = (p.nx + bx - 1) / bx;
-    const int64_t blocks = (int64_t)xblocks * p.ny * p.nz;
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if (force)
         step_kernel_rows<S, true, HINT, MASK_FIRST, SR>
-            <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+            <<<row_grid(xblocks, p.ny, p.nz), bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     else
         step_kernel_rows<S, false, HINT, MASK_FIRST, SR>
-            <<<(unsigned)blocks, bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
+            <<<row_grid(xblocks, p.ny, p.nz), bx, 0, st>>>((const S*)A, (S*)B, code, p, xblocks);
     return cudaGetLastError();
 }
 
 // Stochastic rounding (16-bit storage, p.sr): the one-cell kernels (1-3, and
 // 16 with the mask-first bounce-back) and the packed two-cell kernels (13,
-// 15, 17) have a stochastically rounding form; every other variant runs 15
-// (or 1 where the two-cell kernels do not apply).
+// 15, 17, 18) have a stochastically rounding form; the default (0) runs 18,
+// every other variant 15 (or 1 where the two-cell kernels do not apply).
 template <class S>
 static cudaError_t step_sr_t(int variant, const void* A, void* B, const uint8_t* code, const LatticeParams& p,
                              int block, cudaStream_t st) {
@@ -873,6 +881,12 @@ static cudaError_t step_sr_t(int variant, const void* A, void* B, const uint8_t*
         case 17:
             if (pairs_ok) return step_pairs_x2_t<S, 0, 2, true, true>(A, B, code, p, block, st);
             return step_rows_t<S, 0, false, true>(A, B, code, p, block, st);
+        case 18:
+            if (pairs_ok) return step_pairs_x2_row_t<S, 0, true>(A, B, code, p, st);
+            return step_rows_t<S, 0, false, true>(A, B, code, p, block, st);
+        case 0:
+            if (pairs_ok && block == 0) return step_pairs_x2_row_t<S, 0, true>(A, B, code, p, st);
+            [[fallthrough]];
         default:
             if (pairs_ok)
                 return step_pairs_x2_t<S, 0, 2, false, true>(A, B, code, p, variant == 15 || block > 0 ? block : 64,
@@ -945,12 +959,21 @@ static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* co
                 if (pairs_ok) return step_pairs_x2_t<S, 0, 2, true>(A, B, code, p, block, st);
             }
             return step_rows_t<S, 0>(A, B, code, p, block, st);
+        case 18:
+            if constexpr (std::is_same<S, float>::value || sizeof(S) == 2) {
+                if (pairs_ok) return step_pairs_x2_row_t<S, 0>(A, B, code, p, st);
+            }
+            return step_rows_t<S, 0>(A, B, code, p, block, st);
         case 0:
             // measured defaults on GB300 (256^3): FP32 one cell per thread in
             // 64-thread blocks; FP64 two cells per thread; 16-bit storage two
-            // cells per thread collided as a packed FP32 pair, 64 registers
+            // cells per thread collided as a packed FP32 pair, 64 registers,
+            // one block per row where the row fits (variant 18, else 15)
             if constexpr (sizeof(S) == 2) {
-                if (pairs_ok) return step_pairs_x2_t<S, 0, 2>(A, B, code, p, block > 0 ? block : 64, st);
+                if (pairs_ok) {
+                    if (block > 0) return step_pairs_x2_t<S, 0, 2>(A, B, code, p, block, st);
+                    return step_pairs_x2_row_t<S, 0>(A, B, code, p, st);
+                }
             }
             if constexpr (ieee16<S>) {
                 if (p.nx % 4 == 0) return step_quads16_x2_t<S, 0>(A, B, code, p, block > 0 ? block : 32, st);
