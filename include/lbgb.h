@@ -97,8 +97,9 @@ typedef struct lb_options {
                           so a run is reproducible, every step variant and
                           batch slot gives bitwise the same result, and a
                           checkpoint restores the stream with the step
-                          count.  Supported by step variants 1-3, 13, 15,
-                          16, 17, 18 and the in-place kernels; other variants
+                          count.  Supported by step variants 1-3, 13, 15-19
+                          and the in-place kernels; the default runs 18 (15
+                          where the row does not fit it), other variants
                           run 15 (1 where it does not apply).  Equilibrium
                           initialisation and population import round to
                           nearest even. */
@@ -243,7 +244,7 @@ int lb_get_populations_at(lb_lattice *h, const int64_t *cells, int n, double *ou
  * media), a little slower elsewhere; 16 caps blocks at 128 threads;
  * 18 as 15 with one block per row, the values crossing a warp edge passed
  * through shared memory (nx % 64 == 0 and nx <= 1024, else 15; block size
- * fixed at nx / 2).
+ * fixed at nx / 2); 19 as 18 with the reordered bounce-back of 17 (else 17).
  * A variant that does not apply to the lattice runs
  * variant 1.  In-place lattices have their own two kernels (see
  * lb_options.inplace: variant 2 two cells per thread, others one).

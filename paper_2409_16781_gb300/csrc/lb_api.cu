@@ -514,7 +514,7 @@ int lb_checkpoint_load(lb_lattice* h, const void* host, size_t bytes) {
 
 int lb_set_kernel(lb_lattice* h, int variant, int block) {
     if (!h) return fail(LB_EINVAL, "lb_set_kernel: NULL handle");
-    if (variant < 0 || variant > 18 || block < 0 || block > 1024)
+    if (variant < 0 || variant > 19 || block < 0 || block > 1024)
         return fail(LB_EINVAL, "lb_set_kernel: bad variant %d / block %d", variant, block);
     h->kernel = variant;
     h->block = block;
@@ -610,6 +610,7 @@ int lb_autotune(lb_lattice* h, int reps, int* variant, int* block, float* ms_per
         for (int b : {64, 128}) add(15, b);
         if (h->nx % 64 == 0 && h->nx <= 1024) add(18, 0);
         if (h->walls) add(17, 64);
+        if (h->walls && h->nx % 64 == 0 && h->nx <= 1024) add(19, 0);
     }
     if (h->walls) {
         for (int b : {64, 128}) add(16, b);

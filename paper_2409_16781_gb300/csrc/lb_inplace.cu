@@ -50,6 +50,9 @@ __device__ __forceinline__ typename Vec2<S>::T pack_vals(S a, S b) {
 // follow it) only so that the compiler does not keep the 19 load addresses
 // live through the collision to reuse them for the stores: it recomputes the
 // store addresses instead, which leaves more registers for more warps.
+// Every slot of the array is loaded and then stored by one thread only (the
+// 19 values a thread reads are the 19 slots it writes), so the two-cell
+// kernel loads through the read-only path (ld_pop HINT 3).
 template <class S, bool FORCE, int FORM, bool SR>
 __global__ void __launch_bounds__(512) step_kernel_inplace(const S* Ar, S* Aw, const uint8_t* __restrict__ code,
                                                            LatticeParams p, int xblocks) {
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(ROW ? 512 : 128, ROW ? 2 : 8)
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             float a, b;
-            split2<S>(ld_pop<0>(reinterpret_cast<const V*>(Ar + (int64_t)i * p.ps + cell0)), a, b);
+            split2<S>(ld_pop<3>(reinterpret_cast<const V*>(Ar + (int64_t)i * p.ps + cell0)), a, b);
             d[i] = f32x2(a, b);
         }
     } else {
@@ -122,10 +125,10 @@ __global__ void __launch_bounds__(ROW ? 512 : 128, ROW ? 2 : 8)
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const S* rowp = Ar + (int64_t)D3Q19::opp(i) * p.ps + yo[D3Q19::cy(i) + 1] + zo[D3Q19::cz(i) + 1];
-            v[i] = ld_pop<0>(reinterpret_cast<const V*>(rowp + x0));
+            v[i] = ld_pop<3>(reinterpret_cast<const V*>(rowp + x0));
             if constexpr (!ROW) {
-                if (D3Q19::cx(i) == 1 && own_prev && active) e[i] = ld_pop<0>(rowp + xprev);
-                if (D3Q19::cx(i) == -1 && own_next && active) e[i] = ld_pop<0>(rowp + xnext);
+                if (D3Q19::cx(i) == 1 && own_prev && active) e[i] = ld_pop<3>(rowp + xprev);
+                if (D3Q19::cx(i) == -1 && own_next && active) e[i] = ld_pop<3>(rowp + xnext);
             }
         }
         if constexpr (ROW) {
@@ -210,13 +213,15 @@ __global__ void __launch_bounds__(ROW ? 512 : 128, ROW ? 2 : 8)
         else st_pop<0>(reinterpret_cast<V*>(q), pair_word(i));
     };
     if constexpr (FORM == FORM_STREAMED) {
-        // -> FORM_SWAPPED: P_i(x) into plane opp(i) at x
+        // -> FORM_SWAPPED: P_i(x) into plane opp(i) at x (the pair test
+        // once, outside the loop over directions)
+        if (f0 && f1) {
 #pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            S* q = Aw + (int64_t)D3Q19::opp(i) * p.ps + cell0;
-            if (f0 && f1) {
-                pair_store(q, i);
-            } else {
+            for (int i = 0; i < Q; ++i) pair_store(Aw + (int64_t)D3Q19::opp(i) * p.ps + cell0, i);
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                S* q = Aw + (int64_t)D3Q19::opp(i) * p.ps + cell0;
                 if (f0) st_pop<0>(q, R.one(d[i].v.x, key, cell0, i));
                 if (f1) st_pop<0>(q + 1, R.one(d[i].v.y, key, cell0 + 1, i));
             }

@@ -58,7 +58,11 @@ __device__ __forceinline__ void block_row(int xblocks, int ny, int& xb, int& y, 
 
 // Global loads/stores of population values with a cache policy:
 //   HINT 0: default (L1 + L2),  1: streaming (.cs, evict-first),
-//   HINT 2: L2 only for loads (.cg), streaming stores.
+//   HINT 2: L2 only for loads (.cg), streaming stores,
+//   HINT 3: loads through the read-only (non-coherent) path, default stores
+//           -- for arrays that the launch also writes, valid only where
+//           every location a thread loads is written by no other thread of
+//           the launch and by this thread only after the load.
 template <int HINT, class S>
 __device__ __forceinline__ S ld_pop(const S* p) {
     if constexpr (std::is_same<S, f32d>::value) {
@@ -78,6 +82,7 @@ __device__ __forceinline__ S ld_pop(const S* p) {
 #endif
         if constexpr (HINT == 1) return __ldcs(p);
         else if constexpr (HINT == 2) return __ldcg(p);
+        else if constexpr (HINT == 3) return __ldg(p);
         else return *p;
     }
 }
@@ -98,7 +103,7 @@ __device__ __forceinline__ void st_pop(S* p, S v) {
             }
         }
 #endif
-        if constexpr (HINT == 0) *p = v;
+        if constexpr (HINT == 0 || HINT == 3) *p = v;
         else __stcs(p, v);
     }
 }

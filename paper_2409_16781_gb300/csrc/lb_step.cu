@@ -389,6 +389,8 @@ static cudaError_t step_quads16_t(const void* A, void* B, const uint8_t* code, c
 //   18: variant 15 with whole-row blocks (nx a multiple of 64, at most 1024;
 //       else variant 15): the values that cross a warp edge come from the
 //       neighbouring warp through shared memory (ROW of pair_x2_update).
+//   19: variant 18 with the mask-first bounce-back fix-up (17 where the row
+//       does not fit).
 template <class S, bool FORCE, int HINT, int MINB, bool MASK_FIRST = false, bool SR = false, bool ROW = false>
 __global__ void __launch_bounds__(ROW ? 512 : 256 / MINB, ROW ? 2 : (MINB == 1 ? 0 : 4 * MINB))
     step_kernel_pairs_x2(const S* __restrict__ A, S* __restrict__ B, const uint8_t* __restrict__ code, LatticeParams p,
@@ -422,18 +424,20 @@ static cudaError_t step_pairs_x2_t(const void* A, void* B, const uint8_t* code, 
     return cudaGetLastError();
 }
 
-// Variant 18: one block per row, nx / 2 threads (variant 15 where the row
-// does not fit whole warps or one block).
-template <class S, int HINT, bool SR = false>
+// Variants 18 and 19 (19: with MASK_FIRST): one block per row, nx / 2
+// threads (variant 15, or 17, where the row does not fit whole warps or one
+// block).
+template <class S, int HINT, bool SR = false, bool MASK_FIRST = false>
 static cudaError_t step_pairs_x2_row_t(const void* A, void* B, const uint8_t* code, const LatticeParams& p,
                                        cudaStream_t st) {
-    if (p.nx % 64 != 0 || p.nx > 1024) return step_pairs_x2_t<S, HINT, 2, false, SR>(A, B, code, p, 64, st);
+    if (p.nx % 64 != 0 || p.nx > 1024)
+        return step_pairs_x2_t<S, HINT, 2, MASK_FIRST, SR>(A, B, code, p, 64, st);
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if (force)
-        step_kernel_pairs_x2<S, true, HINT, 2, false, SR, true>
+        step_kernel_pairs_x2<S, true, HINT, 2, MASK_FIRST, SR, true>
             <<<row_grid(1, p.ny, p.nz), p.nx / 2, 0, st>>>((const S*)A, (S*)B, code, p, 1);
     else
-        step_kernel_pairs_x2<S, false, HINT, 2, false, SR, true>
+        step_kernel_pairs_x2<S, false, HINT, 2, MASK_FIRST, SR, true>
             <<<row_grid(1, p.ny, p.nz), p.nx / 2, 0, st>>>((const S*)A, (S*)B, code, p, 1);
     return cudaGetLastError();
 }
@@ -864,7 +868,7 @@ static cudaError_t step_rows_t(const void* A, void* B, const uint8_t* code, cons
 
 // Stochastic rounding (16-bit storage, p.sr): the one-cell kernels (1-3, and
 // 16 with the mask-first bounce-back) and the packed two-cell kernels (13,
-// 15, 17, 18) have a stochastically rounding form; the default (0) runs 18,
+// 15, 17, 18, 19) have a stochastically rounding form; the default (0) runs 18,
 // every other variant 15 (or 1 where the two-cell kernels do not apply).
 template <class S>
 static cudaError_t step_sr_t(int variant, const void* A, void* B, const uint8_t* code, const LatticeParams& p,
@@ -883,6 +887,9 @@ static cudaError_t step_sr_t(int variant, const void* A, void* B, const uint8_t*
             return step_rows_t<S, 0, false, true>(A, B, code, p, block, st);
         case 18:
             if (pairs_ok) return step_pairs_x2_row_t<S, 0, true>(A, B, code, p, st);
+            return step_rows_t<S, 0, false, true>(A, B, code, p, block, st);
+        case 19:
+            if (pairs_ok) return step_pairs_x2_row_t<S, 0, true, true>(A, B, code, p, st);
             return step_rows_t<S, 0, false, true>(A, B, code, p, block, st);
         case 0:
             if (pairs_ok && block == 0) return step_pairs_x2_row_t<S, 0, true>(A, B, code, p, st);
@@ -960,8 +967,11 @@ static cudaError_t step_t(int variant, const void* A, void* B, const uint8_t* co
             }
             return step_rows_t<S, 0>(A, B, code, p, block, st);
         case 18:
+        case 19:
             if constexpr (std::is_same<S, float>::value || sizeof(S) == 2) {
-                if (pairs_ok) return step_pairs_x2_row_t<S, 0>(A, B, code, p, st);
+                if (pairs_ok)
+                    return variant == 18 ? step_pairs_x2_row_t<S, 0>(A, B, code, p, st)
+                                         : step_pairs_x2_row_t<S, 0, false, true>(A, B, code, p, st);
             }
             return step_rows_t<S, 0>(A, B, code, p, block, st);
         case 0:

@@ -75,7 +75,7 @@ def _run(lib, nx, ny, nz, storage, inplace, force, flags, rho, u, schedule):
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16s", "bf16s", "f32d", "e3m12s"])
 def test_every_access_inside_its_array(libs, storage, inplace):
     plain, checked = libs
-    variants = range(19) if not inplace else (0, 1, 2)
+    variants = range(20) if not inplace else (0, 1, 2)
     schedule = [(v, b) for v in variants for b in (0, 32, 96)]
     _violations(checked)  # reset
     min_checks = 0

@@ -144,12 +144,12 @@ def test_porous_channel_small(storage, kernel, perm):
 
 
 def test_set_kernel_range():
-    """Variants 0..18 are accepted; anything else is rejected before any
+    """Variants 0..19 are accepted; anything else is rejected before any
     launch, and the lattice keeps stepping with its previous choice."""
     gpu = Lattice(10, 6, 4, 0.7, flags=W.random_flags(10, 6, 4, seed=2), storage="f32")
-    for v in range(19):
+    for v in range(20):
         gpu.set_kernel(v, 64)
-    for bad in (-1, 19, 99):
+    for bad in (-1, 20, 99):
         with pytest.raises(RuntimeError):
             gpu.set_kernel(bad, 0)
     gpu.step(3)
@@ -240,7 +240,7 @@ def test_autotune_keeps_state(storage, perm, tmp_path, monkeypatch):
     f0 = gpu.populations()
     v, b, ms = gpu.autotune(reps=3)
     assert np.array_equal(gpu.populations(), f0)
-    assert v in range(1, 19) and b % 32 == 0 and ms > 0
+    assert v in range(1, 20) and b % 32 == 0 and ms > 0
     assert (tmp_path / "tune.json").exists()
     again = Lattice(nx, ny, nz, 0.6, u_lid=(0.05, 0, 0), flags=flags, storage=storage)
     assert again.autotune(reps=3) == (v, b, ms)  # from the cache
@@ -315,7 +315,7 @@ def _farfield_flags(nx, ny, nz, seed):
     return fl
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19])
 @pytest.mark.parametrize("storage", STORAGES)
 def test_farfield_every_variant(storage, kernel, perm):
     """Far-field cells (free stream at u_lid: inflow and outflow planes, and a
@@ -360,19 +360,21 @@ ROW_SHAPES = ((64, 5, 4), (128, 6, 3), (192, 3, 5), (1024, 2, 2))
 
 @pytest.mark.parametrize("rounding", ["nearest", "stochastic"])
 @pytest.mark.parametrize("storage", STORAGES)
-def test_whole_row_variant(storage, rounding, perm):
-    """Variant 18 (one block per row, the values that cross a warp edge and
-    the periodic wrap passed through shared memory) pulls the same values as
-    variant 15, so it must give bitwise the same state -- on rows of one warp
-    (the wrap inside the warp) up to 16 warps, with walls, lid, far field and
-    force, and with an all-fluid periodic lattice -- and match the oracle."""
+@pytest.mark.parametrize("pair", [(18, 15), (19, 17)], ids=["18v15", "19v17"])
+def test_whole_row_variant(storage, rounding, pair, perm):
+    """Variants 18 and 19 (one block per row, the values that cross a warp
+    edge and the periodic wrap passed through shared memory) pull the same
+    values as variants 15 and 17, so they must give bitwise the same state --
+    on rows of one warp (the wrap inside the warp) up to 16 warps, with walls,
+    lid, far field and force, and with an all-fluid periodic lattice -- and
+    match the oracle."""
     if rounding == "stochastic" and storage not in ("f16s", "bf16s", "e3m12s"):
         pytest.skip("stochastic rounding is a 16-bit storage option")
     for k, (nx, ny, nz) in enumerate(ROW_SHAPES + ((128, 4, 4),)):
         flags = None if k == len(ROW_SHAPES) else _farfield_flags(nx, ny, nz, seed=nx + 3)
         rho0, u0 = W.random_fields(nx, ny, nz, seed=11, du=0.05, drho=0.02)
         lats = []
-        for kernel in (18, 15):
+        for kernel in pair:
             lat = Lattice(nx, ny, nz, 0.7, u_lid=(0.04, 0.01, -0.02), flags=flags, storage=storage,
                           force=(1e-4, 0, 0), kernel=kernel, rounding=rounding)
             lat.init_fields(rho0, u0)
