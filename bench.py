@@ -49,8 +49,12 @@ METRIC = "D3Q19 MLUPS & fraction of HBM roofline; batched-serve p50/p99 vs plain
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16s": 2, "bf16s": 2, "f32d": 4, "e3m12s": 2}
 FALLBACK_HBM_GBS = 6800.0
 # the files that make up the step kernel (hashed to tie ncu figures to it)
+# the CUDA sources of the step kernels: shared headers, then the two-array
+# kernels' and the in-place kernels' own files
 STEP_SOURCES = ("lb_common.cuh", "lb_fpconv.cuh", "lb_internal.h", "lb_kernels.cuh", "lb_pairs.cuh", "lb_mbarrier.cuh",
                 "lb_step.cu", "lb_inplace.cu")
+STEP_SOURCES_OF = {"two_arrays": tuple(n for n in STEP_SOURCES if n != "lb_inplace.cu"),
+                   "inplace": tuple(n for n in STEP_SOURCES if n not in ("lb_step.cu", "lb_mbarrier.cuh"))}
 
 
 def bytes_per_update(storage: str) -> int:
@@ -290,12 +294,13 @@ def strip_comments(src: str) -> str:
     return " ".join("".join(out).split())
 
 
-def kernel_source_hash() -> str:
-    """Hash of the step kernels' CUDA code (comments excluded); a committed
-    ncu figure is only reported while it matches the kernels being timed."""
+def kernel_source_hash(kind: str = "two_arrays") -> str:
+    """Hash of the CUDA code (comments excluded) of the two-array or the
+    in-place step kernels (`kind`); a committed ncu figure is only reported
+    while it matches the kernels being timed."""
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2409_16781_gb300", "csrc")
-    for name in STEP_SOURCES:
+    for name in STEP_SOURCES_OF[kind]:
         with open(os.path.join(cs, name), encoding="utf-8") as fh:
             h.update(name.encode() + b"\0" + strip_comments(fh.read()).encode())
     return h.hexdigest()[:16]
@@ -323,7 +328,8 @@ def ncu_figure(profile_key: str, variant=None, field: str = "dram_bytes_per_laun
         with open(p) as fh:
             d = json.load(fh)
         rec = d.get(profile_key)
-        if rec and rec.get("source_hash") == kernel_source_hash():
+        kind = "inplace" if profile_key.endswith("_inplace") else "two_arrays"
+        if rec and rec.get("source_hash") == kernel_source_hash(kind):
             per = rec.get("variants", {})
             hit = per.get(str(variant)) if variant is not None else None
             if hit:

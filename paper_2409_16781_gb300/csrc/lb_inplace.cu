@@ -88,11 +88,26 @@ __global__ void __launch_bounds__(512) step_kernel_inplace(const S* Ar, S* Aw, c
 // thread of the row still has to read, and no other block touches the row's
 // slots.  A row with a solid cell takes the general stores below.
 // ---------------------------------------------------------------------------
-template <class S, bool FORCE, int FORM, bool SR, bool ROW = false>
+//
+// OFF32 (ROW only; the launch chooses it when 19 planes of ps values fit
+// 32-bit element offsets): the load and store addresses of the whole-row
+// path are 32-bit offsets from the array's base, fewer instructions than the
+// 64-bit row pointers.
+//
+// The stores of the all-fluid paths are streaming stores (.cs, evict first):
+// the next step reads the array from its first plane again, long after
+// these lines could still be in L2.
+template <class S, bool FORCE, int FORM, bool SR, bool ROW = false, bool OFF32 = false>
 __global__ void __launch_bounds__(ROW ? 512 : 128, ROW ? 2 : 8)
     step_kernel_inplace_pairs(const S* Ar, S* Aw, const uint8_t* __restrict__ code, LatticeParams p,
                               int xblocks) {
     using V = typename Vec2<S>::T;
+    static_assert(!OFF32 || ROW, "32-bit offsets are a form of the whole-row path");
+    // element i of plane `plane`, row offset `rowoff`, x = `x`
+    auto at = [&](int plane, int rowoff, int x) -> int64_t {
+        if constexpr (OFF32) return (int64_t)(uint32_t)((uint32_t)plane * (uint32_t)p.ps + (uint32_t)(rowoff + x));
+        else return (int64_t)plane * p.ps + rowoff + x;
+    };
     const int nx = p.nx, ny = p.ny, nz = p.nz;
     int xb, y, z;
     block_row(xblocks, ny, xb, y, z);
@@ -125,7 +140,7 @@ __global__ void __launch_bounds__(ROW ? 512 : 128, ROW ? 2 : 8)
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             const S* rowp = Ar + (int64_t)D3Q19::opp(i) * p.ps + yo[D3Q19::cy(i) + 1] + zo[D3Q19::cz(i) + 1];
-            v[i] = ld_pop<3>(reinterpret_cast<const V*>(rowp + x0));
+            v[i] = ld_pop<3>(reinterpret_cast<const V*>(Ar + at(D3Q19::opp(i), yo[D3Q19::cy(i) + 1] + zo[D3Q19::cz(i) + 1], x0)));
             if constexpr (!ROW) {
                 if (D3Q19::cx(i) == 1 && own_prev && active) e[i] = ld_pop<3>(rowp + xprev);
                 if (D3Q19::cx(i) == -1 && own_next && active) e[i] = ld_pop<3>(rowp + xnext);
@@ -208,9 +223,9 @@ __global__ void __launch_bounds__(ROW ? 512 : 128, ROW ? 2 : 8)
         if constexpr (SR) return R.two(d[i].v.x, d[i].v.y, key, i);
         else return pack2<S>(d[i].v.x, d[i].v.y);
     };
-    auto pair_store = [&](S* q, int i) {
-        if constexpr (SR) st_pop<0>(reinterpret_cast<uint32_t*>(q), pair_word(i));
-        else st_pop<0>(reinterpret_cast<V*>(q), pair_word(i));
+    auto pair_store = [&](S* q, int i) {  // all-fluid pairs only: streaming stores
+        if constexpr (SR) st_pop<1>(reinterpret_cast<uint32_t*>(q), pair_word(i));
+        else st_pop<1>(reinterpret_cast<V*>(q), pair_word(i));
     };
     if constexpr (FORM == FORM_STREAMED) {
         // -> FORM_SWAPPED: P_i(x) into plane opp(i) at x (the pair test
@@ -279,8 +294,7 @@ __global__ void __launch_bounds__(ROW ? 512 : 128, ROW ? 2 : 8)
                     kp = km = 0;
 #pragma unroll
                     for (int i = 0; i < Q; ++i) {
-                        uint32_t* q = reinterpret_cast<uint32_t*>(Aw + (int64_t)i * p.ps + yt[D3Q19::cy(i) + 1] +
-                                                                  zt[D3Q19::cz(i) + 1] + x0);
+                        uint32_t* q = reinterpret_cast<uint32_t*>(Aw + at(i, yt[D3Q19::cy(i) + 1] + zt[D3Q19::cz(i) + 1], x0));
                         uint32_t v = w[i];
                         if (D3Q19::cx(i) == 1) {  // slots (x0, x0 + 1) <- (x0 - 1, x0)
                             uint32_t pw = __shfl_up_sync(0xffffffffu, w[i], 1);
@@ -293,7 +307,7 @@ __global__ void __launch_bounds__(ROW ? 512 : 128, ROW ? 2 : 8)
                             ++km;
                             v = __byte_perm(w[i], nw, 0x5432);
                         }
-                        st_pop<0>(q, v);
+                        st_pop<1>(q, v);
                     }
                     return;
                 }
@@ -354,12 +368,16 @@ static cudaError_t step_inplace_pairs_form(void* A, const uint8_t* code, const L
     const bool force = p.g[0] != 0.0 || p.g[1] != 0.0 || p.g[2] != 0.0;
     if constexpr (sizeof(S) == 2 && FORM == FORM_SWAPPED) {
         if (p.nx % 64 == 0 && p.nx <= 1024) {  // one block per row, nx/2 threads
-            if (force)
-                step_kernel_inplace_pairs<S, true, FORM, SR, true>
-                    <<<row_grid(1, p.ny, p.nz), p.nx / 2, 0, st>>>((const S*)A, (S*)A, code, p, 1);
+            const dim3 g = row_grid(1, p.ny, p.nz);
+            const bool off32 = (uint64_t)Q * (uint64_t)p.ps <= 0xFFFFFFFFull;
+            if (force && off32)
+                step_kernel_inplace_pairs<S, true, FORM, SR, true, true><<<g, p.nx / 2, 0, st>>>((const S*)A, (S*)A, code, p, 1);
+            else if (force)
+                step_kernel_inplace_pairs<S, true, FORM, SR, true><<<g, p.nx / 2, 0, st>>>((const S*)A, (S*)A, code, p, 1);
+            else if (off32)
+                step_kernel_inplace_pairs<S, false, FORM, SR, true, true><<<g, p.nx / 2, 0, st>>>((const S*)A, (S*)A, code, p, 1);
             else
-                step_kernel_inplace_pairs<S, false, FORM, SR, true>
-                    <<<row_grid(1, p.ny, p.nz), p.nx / 2, 0, st>>>((const S*)A, (S*)A, code, p, 1);
+                step_kernel_inplace_pairs<S, false, FORM, SR, true><<<g, p.nx / 2, 0, st>>>((const S*)A, (S*)A, code, p, 1);
             return cudaGetLastError();
         }
     }

@@ -61,9 +61,21 @@ def test_ncu_figures_need_the_current_sources(monkeypatch):
         t = json.load(fh)
     current = t["step_f32_tgv256"]["source_hash"] == bench.kernel_source_hash()
     assert (bench.ncu_traffic("step_f32_tgv256", 1) is not None) == current
-    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda kind="two_arrays": "0" * 16)
     assert bench.ncu_traffic("step_f32_tgv256", 1) is None
     assert bench.fp64_alu_roofline("f64", 4, 3.5) is None
+
+
+def test_source_hash_per_kernel_family():
+    """The two-array figures depend on the two-array kernels' sources only,
+    the in-place figures on the in-place kernels' only; both on the shared
+    headers."""
+    two, inp = bench.STEP_SOURCES_OF["two_arrays"], bench.STEP_SOURCES_OF["inplace"]
+    assert "lb_step.cu" in two and "lb_inplace.cu" not in two
+    assert "lb_inplace.cu" in inp and "lb_step.cu" not in inp
+    for shared in ("lb_common.cuh", "lb_kernels.cuh", "lb_pairs.cuh", "lb_fpconv.cuh", "lb_internal.h"):
+        assert shared in two and shared in inp
+    assert bench.kernel_source_hash("two_arrays") != bench.kernel_source_hash("inplace")
 
 
 def test_step_sources_exist_and_cover_the_step_code():
