@@ -108,3 +108,13 @@ def test_source_hash_ignores_comments_only():
     assert s('const char* p = "// not a comment"; char q = \'/\';') == \
         'const char* p = "// not a comment"; char q = \'/\';'
     assert s('x = "a\\"b // c"; y;') == 'x = "a\\"b // c"; y;'
+
+
+def test_configs_sections_skip_past_the_deadline(monkeypatch):
+    """A configs section that would start after --configs-deadline-s is
+    reported as skipped (no GPU work), so the line is still printed."""
+    args = bench.parse_args(["--configs-deadline-s", "-1"])
+    out = bench.configs_section(args)
+    for name in ("porous_512", "cavity_768_precision", "serving_2000"):
+        assert "skipped" in out[name], out[name]
+    assert "wall_s" in out
