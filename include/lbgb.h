@@ -175,7 +175,12 @@ int lb_create_in(lb_lattice **out, int nx, int ny, int nz, double tau,
                  void *device_buffer, size_t bytes);
 
 /* Set every cell to the equilibrium f^eq(rho, u) of Eq. 2-3.
- *   rho  host, N doubles (NULL = 1);  u  host, 3N doubles SoA (NULL = 0). */
+ *   rho  host, N doubles (NULL = 1);  u  host, 3N doubles SoA (NULL = 0).
+ * Buffers in page-locked host memory that is mapped into the device's
+ * address space (cudaHostAlloc / cudaMallocHost, or registered as mapped;
+ * both ends of each buffer are checked) are read by the kernel in place, in
+ * one launch; other host memory goes through the library's staging area in
+ * chunks.  Same result either way; synchronises the lattice's stream. */
 int lb_init_fields(lb_lattice *h, const double *rho, const double *u);
 
 /* Advance n >= 0 time steps: each is one fused pull-collide launch
@@ -186,7 +191,10 @@ int lb_step(lb_lattice *h, int n);
 /* Macroscopic fields of the current state: rho and u (half-force shifted,
  * u = (sum_i f_i c_i)/rho + g/2) of the streamed populations at every fluid
  * cell; solid cells report rho = 0, u = 0.
- *   rho  host, N doubles;  u  host, 3N doubles SoA.  Either may be NULL. */
+ *   rho  host, N doubles;  u  host, 3N doubles SoA.  Either may be NULL.
+ * Mapped page-locked host buffers (as for lb_init_fields) are written by the
+ * kernel in place, in one launch; other host memory through the staging
+ * area in chunks.  Synchronises the lattice's stream. */
 int lb_moments(lb_lattice *h, double *rho, double *u);
 
 /* As lb_moments, into device buffers (N and 3N doubles), asynchronous. */

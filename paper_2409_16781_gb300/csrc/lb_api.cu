@@ -296,6 +296,32 @@ int lb_create_in(lb_lattice** out, int nx, int ny, int nz, double tau, const dou
     return create_common(out, nx, ny, nz, tau, u_lid, flags, opt, device_buffer, bytes);
 }
 
+// Device address of a host buffer of `bytes` bytes that the GPU can read and
+// write directly -- page-locked host memory mapped into the device's address
+// space (cudaHostAlloc / cudaMallocHost, or registered as mapped) -- or
+// nullptr for anything else (pageable memory, or a range whose first and last
+// bytes are not one contiguous mapping).  The kernels then move the fields
+// between host memory and HBM themselves, in one launch over the lattice,
+// instead of staging them chunk by chunk.
+static void* mapped_host(const void* ptr, size_t bytes) {
+    if (!ptr || bytes == 0) return nullptr;
+    cudaPointerAttributes first{}, last{};
+    if (cudaPointerGetAttributes(&first, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (first.type != cudaMemoryTypeHost || !first.devicePointer) return nullptr;
+    const char* end = static_cast<const char*>(ptr) + (bytes - 1);
+    if (cudaPointerGetAttributes(&last, end) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (last.type != cudaMemoryTypeHost || static_cast<char*>(last.devicePointer) !=
+                                               static_cast<char*>(first.devicePointer) + (bytes - 1))
+        return nullptr;
+    return first.devicePointer;
+}
+
 int lb_init_fields(lb_lattice* h, const double* rho, const double* u) {
     if (!h) return fail(LB_EINVAL, "lb_init_fields: NULL handle");
     const size_t per_cell = (rho ? 8 : 0) + (u ? 24 : 0);
@@ -305,6 +331,18 @@ int lb_init_fields(lb_lattice* h, const double* rho, const double* u) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (h->inplace) h->form = FORM_SWAPPED;
         return e == cudaSuccess ? LB_OK : cuda_fail(e, "lb_init_fields");
+    }
+    {
+        // mapped host buffers: one launch reads them in place
+        const double* mrho = rho ? (const double*)mapped_host(rho, (size_t)h->N * 8) : nullptr;
+        const double* mu = u ? (const double*)mapped_host(u, (size_t)h->N * 24) : nullptr;
+        if ((!rho || mrho) && (!u || mu)) {
+            cudaError_t e = launch_init(h->storage, h->pop[h->cur], h->pop[1 - h->cur], h->ps, mrho, mu, h->N, 0,
+                                        h->N, h->stream, h->inplace);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (h->inplace) h->form = FORM_SWAPPED;
+            return e == cudaSuccess ? LB_OK : cuda_fail(e, "lb_init_fields");
+        }
     }
     const int64_t chunk = chunk_cells(h, per_cell);
     double* st = (double*)h->staging;
@@ -358,9 +396,20 @@ int lb_moments_device(lb_lattice* h, double* rho_dev, double* u_dev) {
 int lb_moments(lb_lattice* h, double* rho, double* u) {
     if (!h) return fail(LB_EINVAL, "lb_moments: NULL handle");
     if (!rho && !u) return LB_OK;
+    const LatticeParams p = params_of(h);
+    {
+        // mapped host buffers: one launch writes them in place
+        double* mrho = rho ? (double*)mapped_host(rho, (size_t)h->N * 8) : nullptr;
+        double* mu = u ? (double*)mapped_host(u, (size_t)h->N * 24) : nullptr;
+        if ((!rho || mrho) && (!u || mu)) {
+            cudaError_t e = launch_moments(h->storage, h->pop[h->cur], h->code, p, mrho, mu, h->N, 0, h->N,
+                                           h->stream, h->form);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            return e == cudaSuccess ? LB_OK : cuda_fail(e, "lb_moments");
+        }
+    }
     const int64_t chunk = chunk_cells(h, 32);
     double* st = (double*)h->staging;
-    const LatticeParams p = params_of(h);
     for (int64_t c0 = 0; c0 < h->N; c0 += chunk) {
         const int64_t cnt = (h->N - c0 < chunk) ? h->N - c0 : chunk;
         cudaError_t e =

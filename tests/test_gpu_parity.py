@@ -388,3 +388,42 @@ def test_whole_row_variant(storage, rounding, pair, perm):
             check_pair(ora, lats[0], storage, perm, flags)
         for lat in lats:
             lat.close()
+
+
+@pytest.mark.parametrize("inplace", [False, True], ids=["two_arrays", "in_place"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16s"])
+def test_pinned_host_fields_same_as_pageable(storage, inplace):
+    """lb_init_fields and lb_moments read and write mapped page-locked host
+    buffers in place (one launch) and other host memory through the staging
+    area in chunks: both give bitwise the same populations and fields, with
+    either field omitted too."""
+    import ctypes
+
+    import torch
+    nx, ny, nz = 70, 9, 7
+    flags = _farfield_flags(nx, ny, nz, seed=5)
+    rho0, u0 = W.random_fields(nx, ny, nz, seed=13, du=0.05, drho=0.02)
+    rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+    u0 = np.ascontiguousarray(u0, dtype=np.float64)
+    rho_p = torch.from_numpy(rho0.copy()).pin_memory()
+    u_p = torch.from_numpy(u0.copy()).pin_memory()
+    vp = lambda t: ctypes.c_void_p(t.data_ptr())
+    for with_rho, with_u in ((True, True), (True, False), (False, True)):
+        lats = [Lattice(nx, ny, nz, 0.7, u_lid=(0.04, 0.0, 0.01), flags=flags, storage=storage,
+                        force=(1e-4, 0, 0), inplace=inplace) for _ in range(2)]
+        lats[0].init_fields(rho0 if with_rho else None, u0 if with_u else None)   # pageable
+        assert lats[1].lib.lb_init_fields(lats[1].handle, vp(rho_p) if with_rho else None,
+                                          vp(u_p) if with_u else None) == 0       # mapped, in place
+        assert np.array_equal(lats[0].populations(), lats[1].populations())
+        for lat in lats:
+            lat.step(7)
+        rho_a, u_a = lats[0].moments()
+        rho_o = torch.full((nz, ny, nx), -1.0, dtype=torch.float64).pin_memory()
+        u_o = torch.full((3, nz, ny, nx), -1.0, dtype=torch.float64).pin_memory()
+        assert lats[1].lib.lb_moments(lats[1].handle, vp(rho_o), vp(u_o)) == 0
+        assert np.array_equal(rho_o.numpy(), rho_a) and np.array_equal(u_o.numpy(), u_a)
+        u_o.fill_(-1.0)
+        assert lats[1].lib.lb_moments(lats[1].handle, None, vp(u_o)) == 0
+        assert np.array_equal(u_o.numpy(), u_a)
+        for lat in lats:
+            lat.close()
